@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Benchmark of the FSLBM time step (stream-collide, free boundary, mass
+exchange, conversion, LSQR curvature) on the 256^3 oscillating droplet.
+
+Prints one JSON line (rank 0).  `value` is whole-job fluid-cell updates per
+second (MLUPS over liquid + interface cells) with the state resident in HBM;
+each timed step is bracketed by CUDA events on the launching stream and L2 is
+flushed (256 MiB write) before every step, outside the timed interval.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fsl|reference]
+
+Multi-GPU: one process per GPU (torchrun); every rank advances an independent
+replica (its own seeded droplet), so the work per GPU is fixed (weak scaling)
+and there is no data-path collective; only the timing is reduced (max).
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload (the droplet cropped to its bounding box) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FSLBM MLUPS & curvature evals/s at 256^3 at stated κ error vs FP64 oracle"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="fsl", choices=["fsl", "reference"])
+    ap.add_argument("--workload", default="oscillating256")
+    ap.add_argument("--curv", default="lsqr", choices=["lsqr", "fd", "none"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.rows = []
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+
+    def summary(self, t0: float, t1: float) -> dict:
+        rows = [(t, r.split(", ")) for t, r in self.rows]
+        rows = [(t, r) for t, r in rows if len(r) >= 9]
+        inside = [r for t, r in rows if t0 <= t <= t1 + 0.06]
+        note = "samples during the timed region"
+        if not inside and rows:
+            inside = [min(rows, key=lambda tr: min(abs(tr[0] - t0), abs(tr[0] - t1)))[1]]
+            note = "timed region shorter than the sampling interval: nearest sample"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "nvidia-smi unavailable"}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in inside if num(r[1]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in inside:
+            for k, n in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(inside[0][2]),
+                "power_w_max": max((num(r[3]) or 0.0) for r in inside), "reasons": sorted(reasons),
+                "samples": len(inside), "note": note}
+
+
+# ---------------------------------------------------------------- workload
+def geometry_kwargs(g: dict) -> dict:
+    kw = dict(c=g.get("c", (0, 0, 0)), R=g.get("R", 0.0), eps2=g.get("eps2", 0.0), c2=g.get("c2", (0, 0, 0)),
+              R2=g.get("R2", 0.0), zw=g.get("zw", 0.0), h0=g.get("h0", 0.0), amp=g.get("amp", 0.0),
+              wavelength=g.get("wavelength", 1.0), sub=16)
+    if g["kind"] == "mode2":
+        kw["R"] = g["R_s"]
+    return kw
+
+
+def make_sim(F, w, curv, storage, stream):
+    import torch
+    coll = F.TRT if w["collision"] == "trt" else F.BGK
+    cm = {"lsqr": F.CURV_LSQR, "fd": F.CURV_FD, "none": F.CURV_NONE}[curv]
+    st = {"f32": F.F32, "f16": F.F16_OFS, "bf16": F.BF16_OFS}[storage]
+    P = F.make_params(w["shape"], collision=coll, curv_model=cm, storage=st, tau=w["tau"], sigma=w["sigma"],
+                      theta=w["theta"])
+    phi0 = torch.zeros(w["shape"], dtype=torch.float32, device="cuda")
+    F.fill_geometry(P, F.make_geometry(w["geometry"]["kind"], **geometry_kwargs(w["geometry"])), phi0, stream)
+    obs = None
+    if w["walls"]:
+        from paper_1509_07691_gb300 import synthetic as S
+        obs = torch.from_numpy(S.obstacle_mask(w["shape"], w["walls"])).cuda()
+    sim = F.Sim(P, phi0=phi0, obstacle=obs, stream=stream)
+    return P, sim, phi0, obs
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(w, max_seconds: float, gpu_state=None):
+    """Time the FP64 oracle on the droplet cropped to its bounding box (all
+    fluid cells of the workload, gas margin 4) on the host cores; optionally
+    compare the curvature of a GPU state with the oracle's on sampled cells."""
+    import oracle as orc
+    g = w["geometry"]
+    R_out = g.get("R_s", g.get("R", 8.0)) * (1 + abs(g.get("eps2", 0.0))) + 1.0
+    c = np.array(g["c"])
+    lo = np.floor(c - R_out - 4).astype(int)
+    hi = np.ceil(c + R_out + 4).astype(int) + 1
+    ext = hi - lo  # (x, y, z)
+    shape = (int(ext[2]), int(ext[1]), int(ext[0]))
+    kw = geometry_kwargs(g)
+    kw["c"] = tuple(c - lo)
+    og = orc.geom(g["kind"], **kw)
+    # fill: cells far inside / outside by radial bounds, the band cell by cell with the oracle's sampler
+    zz, yy, xx = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    r = np.sqrt((xx - kw["c"][0]) ** 2 + (yy - kw["c"][1]) ** 2 + (zz - kw["c"][2]) ** 2)
+    e = abs(kw.get("eps2", 0.0))
+    phi = np.where(r + 1.0 < kw["R"] * (1 - 0.5 * e), 1.0, 0.0)
+    band = np.nonzero(((r + 1.0 >= kw["R"] * (1 - 0.5 * e)) & (r - 1.0 <= kw["R"] * (1 + e))).ravel())[0]
+    phi.ravel()[band] = orc.fill_cells(og, shape, band)
+    coll = 1 if w["collision"] == "trt" else 0
+    P = orc.params(shape, collision=coll, tau=w["tau"], sigma=w["sigma"], theta=w["theta"], curv_model=0)
+    st = orc.init_state(P, phi)
+    n_fluid = int(np.count_nonzero(st.flags & 3))
+    steps, t_used = 0, 0.0
+    while t_used < max_seconds and steps < 1000:
+        t0 = time.perf_counter()
+        st, counts, _, _ = orc.step(P, st)
+        t_used += time.perf_counter() - t0
+        steps += 1
+    out = {"value": n_fluid * steps / t_used / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+           "sample": f"{steps} FP64 oracle steps (LSQR curvature + step) of the {w['shape'][2]}^3 droplet cropped "
+                     f"to its bounding box {shape[2]}x{shape[1]}x{shape[0]} ({n_fluid} fluid cells), single thread",
+           "seconds": round(t_used, 3), "steps": steps, "fluid_cells": n_fluid}
+    if gpu_state is not None:
+        out["kappa_check"] = kappa_error(orc, gpu_state, w)
+    return out
+
+
+def kappa_error(orc, gs, w, n_sample=300, half=3):
+    """Oracle LSQR curvature on 7^3 windows (FP32 state cast to FP64) around
+    sampled interface cells vs the GPU curvature of the same state."""
+    flags, phi, kappa = gs["flags"], gs["phi"], gs["kappa"]
+    idx = np.argwhere((flags & 15) == 2)
+    pick = idx[(np.linspace(0, len(idx) - 1, min(n_sample, len(idx)))).astype(int)]
+    errs, refs = [], []
+    P = orc.params((2 * half + 1,) * 3, theta=w["theta"], curv_model=0)
+    for z, y, x in pick:
+        sl = [np.arange(v - half, v + half + 1) % n for v, n in zip((z, y, x), flags.shape)]
+        fw = (flags[np.ix_(*sl)] & 15).astype(np.uint8)
+        pw = phi[np.ix_(*sl)].astype(np.float64)
+        k, _, _ = orc.curvature(P, fw, pw)
+        ref = k[half, half, half]
+        refs.append(ref)
+        errs.append(abs(kappa[z, y, x] - ref))
+    refs, errs = np.array(refs), np.array(errs)
+    L = max(flags.shape)
+    rel = errs / np.maximum(np.abs(refs), 1.0 / L)
+    return {"cells": int(len(pick)), "max_rel": float(rel.max()), "median_rel": float(np.median(rel)),
+            "mean_abs_kappa": float(np.mean(np.abs(refs))), "tolerance": 1e-4,
+            "definition": "|k_gpu - k_fp64| / max(|k_fp64|, 1/L), FP64 oracle LSQR on the same FP32 fill levels"}
+
+
+# ---------------------------------------------------------------- main legs
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    from paper_1509_07691_gb300 import synthetic as S
+    import oracle as orc
+    w = S.workload(args.workload)
+    # warm-up and timed steps on the bounded sample (each step: one oracle step of the cropped droplet)
+    per_step = max(1.0, min(3.0, 150.0 / max(1, args.steps + args.warmup)))
+    base = oracle_sample(w, max_seconds=per_step)
+    value = base["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * base["seconds"] / base["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload} (cropped to the droplet's bounding box)",
+                       "grid": list(w["shape"][::-1])},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": base["sample"]},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_fsl(args):
+    import torch
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1509_07691_gb300 import build as B
+    B.build()
+    from paper_1509_07691_gb300 import fsl as F
+    from paper_1509_07691_gb300 import synthetic as S
+    w = S.workload(args.workload, seed=S.SEED + rank)
+    stream = torch.cuda.current_stream()
+    P, sim, phi0, obs = make_sim(F, w, args.curv, args.storage, stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    st = sim.stats()
+    n_fluid, n_if, N = int(st[0] + st[1]), int(st[1]), sim.N
+
+    # ---- timed region: K steps, each between events; L2 flushed before each
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    time.sleep(0.15)
+    t0 = time.time()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        nf = torch.tensor([n_fluid], dtype=torch.float64, device="cuda")
+        dist.all_reduce(nf)
+        total_fluid = float(nf.item())
+    else:
+        total_fluid = float(n_fluid)
+    ms_per_step = ms / args.steps
+    value = total_fluid * args.steps / (ms * 1e-3) / 1e6
+
+    # ---- per-phase device times (kernel by kernel, same state evolution)
+    nprof = min(args.steps, 50)
+    ph = np.zeros(5)
+    for k in range(nprof):
+        flush.fill_(float(k))
+        ph += sim.step_profile()
+    ph /= nprof
+    clk_prof_end = time.time()
+    clk.stop()
+    clocks = clk.summary(t0, t1)
+
+    # ---- curvature alone (LSQR) on the current state
+    kap = torch.empty_like(sim.kappa)
+    sim.curvature(F.CURV_LSQR, kap)
+    cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    for a, b in cev:
+        flush.fill_(1.0)
+        a.record(stream)
+        sim.curvature(F.CURV_LSQR, kap)
+        b.record(stream)
+    torch.cuda.synchronize()
+    curv_ms = sum(a.elapsed_time(b) for a, b in cev) / len(cev)
+    st2 = sim.stats()
+    n_if_now = int(st2[7])
+
+    # ---- mass reduction (FP64 partials) alone
+    m0 = time.perf_counter()
+    for _ in range(5):
+        sim.mass_total()
+    mass_ms = (time.perf_counter() - m0) * 1e3 / 5
+
+    # ---- end to end through the public API with host buffers
+    phi_host = phi0.cpu().pin_memory()
+    obs_host = obs.cpu().pin_memory() if obs is not None else None
+    sim.close()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    sim2 = F.Sim(P, phi0=phi_host.numpy(), obstacle=None if obs_host is None else obs_host.numpy(), stream=stream)
+    sim2.step(args.steps)
+    mtot, _ = sim2.mass_total()
+    torch.cuda.synchronize()
+    e_s = time.perf_counter() - e0
+    h2d = N * 4 + (N if obs_host is not None else 0)
+    e2e = {"value": n_fluid * args.steps / e_s / 1e6 * (ws if ws > 1 else 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 16 / args.steps,
+           "includes": "fsl_init from pinned host fill levels (upload, types, f = w_q), graph capture, K steps, "
+                       "fsl_mass read back"}
+
+    # ---- roofline of the dominant kernel
+    names = ["normals_plic", "lsqr_curvature", "stream_collide", "convert", "finalize"]
+    dom = int(np.argmax(ph))
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bytes_per = {"stream_collide": 152.0 * n_fluid + 1.0 * N + 100.0 * n_if,
+                 "finalize": 2.0 * N + 16.0 * n_if,
+                 "normals_plic": 16.0 * n_if + 27 * 4.0 * n_if,
+                 "convert": 0.0,
+                 "lsqr_curvature": 26 * 17.0 * n_if}
+    roof = {"kernel": names[dom], "bound": "hbm", "unit": "GB/s",
+            "achieved": bytes_per[names[dom]] / (ph[dom] * 1e-3) / 1e9, "peak": hbm,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst)" if peaks else "fallback 6.8 TB/s",
+            "traffic": None, "algorithmic_bytes": bytes_per[names[dom]]}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    sc_bytes = bytes_per["stream_collide"]
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"f32": "f32", "f16": "f16-offset/f32", "bf16": "bf16-offset/f32"}[args.storage],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "grid": list(w["shape"][::-1]), "geometry": w["geometry"]["kind"],
+                       "R": w["geometry"].get("R"), "sigma": w["sigma"], "tau": w["tau"], "curvature": args.curv,
+                       "storage": args.storage, "l2": "flushed before every timed step (256 MiB write)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "fluid_cells": n_fluid, "interface_cells": n_if, "mlups_domain": N * args.steps / (ms * 1e-3) / 1e6,
+            "curvature_evals_per_s": n_if_now / (curv_ms * 1e-3), "curvature_ms": curv_ms,
+            "phases_ms": dict(zip(names, [round(float(v), 5) for v in ph])),
+            "stream_collide_gbs": sc_bytes / (ph[2] * 1e-3) / 1e9,
+            "mass_reduce_ms": mass_ms, "roofline": roof, "e2e": e2e,
+            "gpu_launches": 5 * args.steps, "clocks": clocks}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        gs = {"flags": sim2.flags_current().cpu().numpy(), "phi": sim2.phi.double().cpu().numpy()}
+        sim2.curvature(F.CURV_LSQR)
+        torch.cuda.synchronize()
+        gs["kappa"] = sim2.kappa.double().cpu().numpy()
+        line["cpu_baseline"] = oracle_sample(w, args.cpu_seconds, gpu_state=gs)
+        line["kappa_err_vs_fp64"] = line["cpu_baseline"].pop("kappa_check")
+    sim2.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_fsl(args)
+
+
+if __name__ == "__main__":
+    main()

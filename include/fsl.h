@@ -1,0 +1,195 @@
+/*
+ * fsl.h -- C ABI of the GB300 (sm_103a) free-surface lattice Boltzmann step
+ * with least-squares and finite-difference curvature (Bogner, Ruede, Harting,
+ * arXiv 1509.07691).
+ *
+ * Memory and ownership
+ *   All field buffers are caller-owned device memory (for instance torch
+ *   tensors), described by fsl_fields.  The library borrows them for the
+ *   lifetime of the context and never frees them.  It allocates nothing on
+ *   the device itself: every piece of scratch lives in the caller's
+ *   workspace buffer (size from fsl_workspace_size).
+ *
+ * Layout (shared with any checker: plain arrays, x fastest)
+ *   cell index   i = x + nx*(y + ny*z), 0 <= i < N = nx*ny*nz.  All three axes
+ *                wrap periodically; walls are cells of type FSL_OBSTACLE.
+ *   PDFs         f[q*N + i], q in the D3Q19 order
+ *                  q  : 0  1  2  3  4  5  6  7  8  9 10 11 12 13 14 15 16 17 18
+ *                  cx : 0  1 -1  0  0  0  0  1 -1  1 -1  1 -1  1 -1  0  0  0  0
+ *                  cy : 0  0  0  1 -1  0  0  1 -1 -1  1  0  0  0  0  1 -1  1 -1
+ *                  cz : 0  0  0  0  0  1 -1  0  0  0  0  1 -1 -1  1  1 -1 -1  1
+ *                stored as float (FSL_F32), or as (f - w_q) * 2^storage_shift in
+ *                IEEE half (FSL_F16_OFS) or bfloat16 (FSL_BF16_OFS).
+ *                Between steps the current buffer holds post-collision values f'.
+ *   flags        one byte per cell: bits 0..3 the cell type (one of the FSL_*
+ *                type values below), bit 4 FSL_NEAR_OBSTACLE (set by the
+ *                library: the cell has an obstacle D3Q19 neighbour), bits 5..7
+ *                zero between steps.  The buffers hold N bytes rounded up to a
+ *                multiple of 4.
+ *   mass, phi    float per cell: mass m and fill level phi = m / rho (meaningful
+ *                at interface cells; phi = 1 at liquid, 0 at gas cells).
+ *   kappa        float per cell: the curvature last computed (interface cells).
+ *
+ * Streams and synchronisation
+ *   Every call enqueues its work on the stream given to fsl_init and returns
+ *   without waiting, except the calls marked "synchronising".
+ *
+ * Errors
+ *   Functions return FSL_OK (0) or a negative code.  Device-side failures set
+ *   a sticky status word that fsl_status reads.  A context is not thread
+ *   safe: use one context per host thread and stream.
+ */
+#ifndef FSL_H
+#define FSL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FSL_OK 0
+#define FSL_EINVAL (-1)       /* invalid parameter, shape or pointer */
+#define FSL_ECUDA (-2)        /* a CUDA runtime call failed */
+#define FSL_ECAPACITY (-3)    /* a device list overflowed (state not advanced) */
+#define FSL_ETIMEOUT (-4)     /* a bounded device wait gave up */
+#define FSL_ENAN (-5)         /* non-finite value found in the state */
+#define FSL_EUNSUPPORTED (-6) /* option not available in this build */
+
+/* cell types (Sec. II: liquid, interface, gas cells; walls are obstacle cells) */
+#define FSL_LIQUID 1
+#define FSL_INTERFACE 2
+#define FSL_GAS 4
+#define FSL_OBSTACLE 8
+#define FSL_TYPE_MASK 15
+#define FSL_NEAR_OBSTACLE 16
+
+typedef struct fsl_ctx fsl_ctx; /* opaque */
+
+enum fsl_collision { FSL_BGK = 0, FSL_TRT = 1 };
+enum fsl_curv_model { FSL_CURV_LSQR = 0, FSL_CURV_FD = 1, FSL_CURV_NONE = 2 };
+enum fsl_storage { FSL_F32 = 0, FSL_F16_OFS = 1, FSL_BF16_OFS = 2 };
+enum fsl_where { FSL_NONE = 0, FSL_HOST = 1, FSL_DEVICE = 2 };
+
+/* Parameters of the method (Sec. II).  All lattice units. */
+typedef struct fsl_params {
+    int32_t nx, ny, nz;     /* grid; each >= 3 */
+    int32_t collision;      /* FSL_BGK or FSL_TRT (two relaxation times) */
+    int32_t curv_model;     /* model used inside fsl_step */
+    int32_t storage;        /* fsl_storage of the PDF buffers */
+    int32_t storage_shift;  /* power-of-two scale of 16-bit offsets (e.g. 8) */
+    int32_t plic_iters;     /* bisection steps of the PLIC offset (e.g. 30) */
+    double tau;             /* relaxation time, nu = (tau - 1/2)/3; > 1/2 */
+    double magic;           /* TRT Lambda = (tau - 1/2)(tau_odd - 1/2), e.g. 3/16 */
+    double sigma;           /* surface tension */
+    double p_gas;           /* gas pressure p_g (1/3 gives rho_b = 1 at sigma = 0) */
+    double theta;           /* equilibrium contact angle theta_eq, radians */
+    double eps_convert;     /* conversion threshold eps, e.g. 1e-3 */
+    double lsqr_fp64_cond;  /* re-solve an LSQR cell in FP64 when max|R_jj|/min|R_jj|
+                               of its FP32 QR exceeds this (1e3: normal equations 1e6) */
+} fsl_params;
+
+/* Caller-owned device buffers (all 256-byte aligned). */
+typedef struct fsl_fields {
+    void *f[2];          /* 19*N PDFs each, element type per params.storage */
+    uint8_t *flags[2];   /* N bytes rounded up to a multiple of 4, each */
+    float *mass;         /* N */
+    float *phi;          /* N */
+    float *kappa;        /* N */
+    void *workspace;     /* fsl_workspace_size(params) bytes */
+} fsl_fields;
+
+/* Geometry of the initial fill levels (Sec. III.A: each cell is sub-divided
+ * sub^3 times and phi is the fraction of sub-cell centres inside the shape). */
+typedef struct fsl_geometry {
+    int32_t kind;     /* 0 sphere |x-c| <= R; 1 P2-perturbed sphere
+                         r <= R (1 + eps2 P2(cos th)); 2 spherical cap: sphere and
+                         z >= zw; 3 union of spheres (c, R) and (c2, R2);
+                         4 pool z < h0 + amp sin(2 pi x/L) sin(2 pi y/L);
+                         5 half-space n.x <= d */
+    int32_t invert;   /* 1: liquid outside the shape (a bubble) */
+    int32_t sub;      /* sub-samples per axis, 1..64 */
+    int32_t pad_;
+    double c[3], R, eps2;
+    double c2[3], R2;
+    double zw;
+    double n[3], d;
+    double h0, amp, wavelength;
+} fsl_geometry;
+
+/* Bytes of workspace the context needs for these parameters. */
+size_t fsl_workspace_size(const fsl_params *params);
+
+/* Fill levels of a geometry by sub-sampling (Sec. III.A), written to phi_dev
+ * (N floats, device).  Sample points are x + (s + 1/2)/sub - 1/2 in each axis;
+ * inside tests run in FP64 without contraction.  Asynchronous on `stream`. */
+int fsl_fill_geometry(const fsl_params *params, const fsl_geometry *geom, float *phi_dev, void *stream);
+
+/* Create a context and set up the initial state (Sec. II):
+ *   phi0       fill levels (N floats) on the host (FSL_HOST), on the device
+ *              (FSL_DEVICE), or FSL_NONE to take fields->phi as it is;
+ *   obstacle   N bytes, nonzero = obstacle cell, host or device, or FSL_NONE;
+ * then types from phi (phi <= 0 gas, >= 1 liquid, else interface; every
+ * liquid cell with a gas neighbour becomes interface), f = w_q, m = phi, and
+ * the interface list.  fields->f[0] / flags[0] hold the state afterwards.
+ * Asynchronous on `stream` (a cudaStream_t, or NULL for the default stream). */
+int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *phi0, int phi0_where,
+             const uint8_t *obstacle, int obstacle_where, void *stream, struct fsl_ctx **out);
+
+/* The caller wrote a state directly into f[parity], flags[parity] (type bits),
+ * mass and phi: recompute the near-obstacle bits and the interface list.
+ * Asynchronous. */
+int fsl_refresh(struct fsl_ctx *ctx);
+
+/* Advance nsteps time steps (Sec. II): curvature kappa(t) of every interface
+ * cell by params.curv_model; pull stream with Eq. (reconstruct) at gas links
+ * (rho_b = 3 p_g + 6 sigma kappa, u_b = u(x,t)) and at contact-line obstacle
+ * links whose outgoing direction points against the interface normal projected
+ * into the wall, bounce-back at other obstacle links; mass exchange Eqs.
+ * (advection1/2); BGK/TRT collision; conversion of interface cells with
+ * m > (1+eps) rho or m < -eps rho, neighbourhood fix and equal sharing of the
+ * excess mass among interface neighbours.  The step sequence is recorded as
+ * a CUDA graph on first use.  Asynchronous. */
+int fsl_step(struct fsl_ctx *ctx, int nsteps);
+
+/* Curvature of the current state by `model` (Sec. II.A FD with K8 smoothing
+ * and wetting normals, Eq. contactNormal; Sec. II.C LSQR paraboloid fit to
+ * PLIC points with contact-point rows/constraints, Eq. contactConstraint),
+ * written to kappa_out (N floats, device; interface cells only; may be
+ * fields->kappa).  Asynchronous. */
+int fsl_curvature(struct fsl_ctx *ctx, int model, float *kappa_out);
+
+/* Total mass sum_interface m + sum_liquid rho, and the mass lost by
+ * conversions with no interface neighbour.  Block partial sums in FP64 are
+ * added in a fixed order.  Synchronising. */
+int fsl_mass(struct fsl_ctx *ctx, double *total_mass, double *lost_mass);
+
+/* counts_out[0..7]: liquid, interface, gas, obstacle cells, interface cells
+ * without a liquid or without a gas neighbour, liquid cells touching gas,
+ * LSQR cells solved in FP64 (last curvature pass), interface list length.
+ * Synchronising. */
+int fsl_stats(struct fsl_ctx *ctx, int64_t counts_out[8]);
+
+/* One time step like fsl_step(ctx, 1), launched kernel by kernel (no graph)
+ * with CUDA events on the context's stream between its phases; ms_out[0..4]
+ * receive the device time of: normals + PLIC, curvature, stream-collide,
+ * conversion, finalize.  For profiling.  Synchronising. */
+int fsl_step_profile(struct fsl_ctx *ctx, float ms_out[5]);
+
+/* Which buffer (0 or 1) of fields->f / flags holds the current state. */
+int fsl_parity(const struct fsl_ctx *ctx);
+
+/* Sticky device status (FSL_OK or an error code).  Synchronising. */
+int fsl_status(struct fsl_ctx *ctx);
+
+const char *fsl_strerror(int code);
+
+/* Release host-side resources and CUDA graphs (not the caller's buffers). */
+void fsl_destroy(struct fsl_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

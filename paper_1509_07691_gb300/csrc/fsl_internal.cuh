@@ -1,0 +1,172 @@
+// fsl_internal.cuh -- device-side building blocks shared by the FSLBM kernels
+// (lattice, cell flags, PDF storage encodings, list appends, kernel argument
+// block).  Internal to libfsl; the public ABI is include/fsl.h.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fsl.h"
+
+namespace fslk {
+
+constexpr int Q = 19;
+
+// D3Q19 lattice (Sec. II), same order as the public header.
+__host__ __device__ __forceinline__ constexpr int cx(int q) {
+    return (q == 1 || q == 7 || q == 9 || q == 11 || q == 13) ? 1
+         : (q == 2 || q == 8 || q == 10 || q == 12 || q == 14) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int cy(int q) {
+    return (q == 3 || q == 7 || q == 10 || q == 15 || q == 17) ? 1
+         : (q == 4 || q == 8 || q == 9 || q == 16 || q == 18) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int cz(int q) {
+    return (q == 5 || q == 11 || q == 14 || q == 15 || q == 18) ? 1
+         : (q == 6 || q == 12 || q == 13 || q == 16 || q == 17) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+__host__ __device__ __forceinline__ constexpr float wq(int q) {
+    return q == 0 ? 1.0f / 3.0f : (q <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+
+// cell flag bits: type (public), near-obstacle (public, static), transient (internal)
+enum : uint8_t {
+    T_LIQ = FSL_LIQUID,
+    T_IF = FSL_INTERFACE,
+    T_GAS = FSL_GAS,
+    T_OBS = FSL_OBSTACLE,
+    T_MASK = FSL_TYPE_MASK,
+    B_NEAR = FSL_NEAR_OBSTACLE,
+    B_TOLIQ = 32,  // interface cell that fills this step
+    B_TOGAS = 64,  // interface cell that empties this step
+    B_NEW = 128,   // gas or liquid cell that becomes interface this step
+};
+
+// device counters in the workspace
+enum { C_IF = 0, C_FILL = 1, C_EMPTY = 2, C_NEWGAS = 3, C_LIQ2IF = 4, C_FP64 = 5, C_NCOUNT = 16 };
+
+// status word values (sticky; first error wins)
+__device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
+
+// kernel argument block (passed by value)
+struct Dev {
+    int nx, ny, nz;
+    long long N;
+    const void *fsrc;  // post-collision PDFs at t
+    void *fdst;        // post-collision PDFs at t+1
+    uint8_t *flags;      // types at t (+ transient bits during a step)
+    uint8_t *flags_next; // types at t+1
+    float *mass, *phi, *kappa, *rho, *excess;
+    float4 *normal;
+    int *iflist, *fill, *empty, *newgas, *liq2if;
+    int *counts;
+    double *lost;
+    int *status;
+    double *partial;
+    long long *stats;
+    // method parameters
+    int collision, storage, plic_iters, curv_model;
+    float omega_e, omega_o;  // 1/tau_even, 1/tau_odd
+    float rho_gas, six_sigma, eps;
+    float cos_theta, sin_theta;
+    float scale, inv_scale;  // 16-bit offset storage
+    float fp64_cond;
+    double cos_theta_d, sin_theta_d;
+};
+
+// ---- PDF storage -----------------------------------------------------------
+template <int S>
+struct Store;
+template <>
+struct Store<FSL_F32> {
+    using T = float;
+    __device__ static __forceinline__ float ld(const void *p, long long k, int q, const Dev &) {
+        return __ldg(static_cast<const float *>(p) + k);
+    }
+    __device__ static __forceinline__ float ldcg(const void *p, long long k, int q, const Dev &) {
+        return __ldcg(static_cast<const float *>(p) + k);
+    }
+    __device__ static __forceinline__ void st(void *p, long long k, int q, float v, const Dev &) {
+        static_cast<float *>(p)[k] = v;
+    }
+};
+template <>
+struct Store<FSL_F16_OFS> {
+    using T = __half;
+    __device__ static __forceinline__ float ld(const void *p, long long k, int q, const Dev &d) {
+        return fmaf(__half2float(__ldg(static_cast<const __half *>(p) + k)), d.inv_scale, wq(q));
+    }
+    __device__ static __forceinline__ float ldcg(const void *p, long long k, int q, const Dev &d) {
+        return fmaf(__half2float(__ldcg(static_cast<const __half *>(p) + k)), d.inv_scale, wq(q));
+    }
+    __device__ static __forceinline__ void st(void *p, long long k, int q, float v, const Dev &d) {
+        static_cast<__half *>(p)[k] = __float2half_rn((v - wq(q)) * d.scale);
+    }
+};
+template <>
+struct Store<FSL_BF16_OFS> {
+    using T = __nv_bfloat16;
+    __device__ static __forceinline__ float ld(const void *p, long long k, int q, const Dev &d) {
+        return fmaf(__bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(p) + k)), d.inv_scale, wq(q));
+    }
+    __device__ static __forceinline__ float ldcg(const void *p, long long k, int q, const Dev &d) {
+        return fmaf(__bfloat162float(__ldcg(static_cast<const __nv_bfloat16 *>(p) + k)), d.inv_scale, wq(q));
+    }
+    __device__ static __forceinline__ void st(void *p, long long k, int q, float v, const Dev &d) {
+        static_cast<__nv_bfloat16 *>(p)[k] = __float2bfloat16_rn((v - wq(q)) * d.scale);
+    }
+};
+
+// ---- indexing ----------------------------------------------------------------
+__device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+__device__ __forceinline__ long long cell_index(const Dev &d, int x, int y, int z) {
+    return (long long)x + (long long)d.nx * ((long long)y + (long long)d.ny * z);
+}
+
+__device__ __forceinline__ long long nbr_index(const Dev &d, int x, int y, int z, int dx, int dy, int dz) {
+    return cell_index(d, wrap(x + dx, d.nx), wrap(y + dy, d.ny), wrap(z + dz, d.nz));
+}
+
+__device__ __forceinline__ void cell_coords(const Dev &d, long long i, int &x, int &y, int &z) {
+    long long row = i / d.nx;
+    x = (int)(i - row * d.nx);
+    z = (int)(row / d.ny);
+    y = (int)(row - (long long)z * d.ny);
+}
+
+// Warp-aggregated append of `value` to `list` when `pred` holds.  Every lane of
+// the warp must call it (no lane may have exited).
+__device__ __forceinline__ void warp_append(int *list, int *count, bool pred, int value) {
+    unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (m == 0) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
+// ---- launch wrappers (defined in the .cu files) -------------------------------
+void launch_fill_geometry(const fsl_params &p, const fsl_geometry &g, float *phi, cudaStream_t s);
+void launch_init_types(const Dev &d, const uint8_t *obstacle, uint8_t *tmp, cudaStream_t s);
+void launch_init_state(const Dev &d, const uint8_t *tmp, cudaStream_t s);
+void launch_refresh(const Dev &d, cudaStream_t s);
+void launch_stats(const Dev &d, cudaStream_t s);
+void launch_mass(const Dev &d, double *out, cudaStream_t s);
+void launch_stream_collide(const Dev &d, cudaStream_t s);
+void launch_convert(const Dev &d, cudaStream_t s);
+void launch_finalize(const Dev &d, cudaStream_t s);
+void launch_normals(const Dev &d, cudaStream_t s);
+void launch_lsqr(const Dev &d, float *kappa_out, cudaStream_t s);
+void launch_fd(const Dev &d, float *kappa_out, cudaStream_t s);
+void launch_zero_kappa(const Dev &d, float *kappa_out, cudaStream_t s);
+
+int max_partials();
+int list_grid(const Dev &d);
+
+}  // namespace fslk

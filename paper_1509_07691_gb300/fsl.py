@@ -1,0 +1,258 @@
+"""Thin Python binding of libfsl (include/fsl.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels.  PyTorch only
+provides the device buffers (caller-owned, as the C ABI requires) and the
+CUDA stream.  If libfsl.so is missing the import of this module fails: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfsl.so")
+
+OK, EINVAL, ECUDA, ECAPACITY, ETIMEOUT, ENAN, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+LIQUID, INTERFACE, GAS, OBSTACLE, TYPE_MASK, NEAR_OBSTACLE = 1, 2, 4, 8, 15, 16
+BGK, TRT = 0, 1
+CURV_LSQR, CURV_FD, CURV_NONE = 0, 1, 2
+F32, F16_OFS, BF16_OFS = 0, 1, 2
+WHERE_NONE, WHERE_HOST, WHERE_DEVICE = 0, 1, 2
+GEOMETRY_KINDS = {"sphere": 0, "mode2": 1, "cap": 2, "two_spheres": 3, "pool": 4, "plane": 5}
+Q = 19
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("collision", ctypes.c_int32), ("curv_model", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("storage_shift", ctypes.c_int32), ("plic_iters", ctypes.c_int32),
+                ("tau", ctypes.c_double), ("magic", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("p_gas", ctypes.c_double), ("theta", ctypes.c_double), ("eps_convert", ctypes.c_double),
+                ("lsqr_fp64_cond", ctypes.c_double)]
+
+
+class Fields(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p * 2), ("flags", ctypes.c_void_p * 2), ("mass", ctypes.c_void_p),
+                ("phi", ctypes.c_void_p), ("kappa", ctypes.c_void_p), ("workspace", ctypes.c_void_p)]
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("invert", ctypes.c_int32), ("sub", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("c", ctypes.c_double * 3), ("R", ctypes.c_double),
+                ("eps2", ctypes.c_double), ("c2", ctypes.c_double * 3), ("R2", ctypes.c_double),
+                ("zw", ctypes.c_double), ("n", ctypes.c_double * 3), ("d", ctypes.c_double),
+                ("h0", ctypes.c_double), ("amp", ctypes.c_double), ("wavelength", ctypes.c_double)]
+
+
+_lib = None
+_SIGNATURES = {
+    "fsl_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(Params)]),
+    "fsl_fill_geometry": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(Geometry), ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "fsl_init": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(Fields), ctypes.c_void_p, ctypes.c_int,
+                                ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "fsl_refresh": (ctypes.c_int, [ctypes.c_void_p]),
+    "fsl_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "fsl_curvature": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "fsl_mass": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "fsl_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "fsl_step_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    "fsl_parity": (ctypes.c_int, [ctypes.c_void_p]),
+    "fsl_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "fsl_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "fsl_destroy": (None, [ctypes.c_void_p]),
+}
+EXPORTED = tuple(_SIGNATURES)
+
+
+def lib():
+    """Load libfsl.so (raises if it has not been built: no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfsl.so not built ({LIB_PATH}); run paper_1509_07691_gb300.build.build()")
+        l = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(l, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = l
+    return _lib
+
+
+class FslError(RuntimeError):
+    pass
+
+
+def check(rc: int, what: str = ""):
+    if rc != OK:
+        msg = lib().fsl_strerror(rc).decode()
+        raise FslError(f"{what}: {msg} ({rc})")
+
+
+def make_params(shape, collision=BGK, curv_model=CURV_LSQR, storage=F32, storage_shift=8, plic_iters=30, tau=1.0,
+                magic=3.0 / 16.0, sigma=0.0, p_gas=1.0 / 3.0, theta=math.pi / 2, eps_convert=1e-3,
+                lsqr_fp64_cond=1e3) -> Params:
+    """shape = (nz, ny, nx) of the numpy/torch arrays (x fastest)."""
+    nz, ny, nx = shape
+    return Params(nx, ny, nz, collision, curv_model, storage, storage_shift, plic_iters, tau, magic, sigma, p_gas,
+                  theta, eps_convert, lsqr_fp64_cond)
+
+
+def make_geometry(kind, c=(0, 0, 0), R=0.0, eps2=0.0, c2=(0, 0, 0), R2=0.0, zw=0.0, n=(0, 0, 1), d=0.0, h0=0.0,
+                  amp=0.0, wavelength=1.0, invert=0, sub=16) -> Geometry:
+    k = GEOMETRY_KINDS[kind] if isinstance(kind, str) else int(kind)
+    D3 = ctypes.c_double * 3
+    return Geometry(k, int(invert), int(sub), 0, D3(*c), R, eps2, D3(*c2), R2, zw, D3(*n), d, h0, amp, wavelength)
+
+
+def _stream_handle(stream) -> int:
+    return 0 if stream is None else int(stream.cuda_stream)
+
+
+def fill_geometry(params: Params, geom: Geometry, phi: torch.Tensor, stream=None):
+    check(lib().fsl_fill_geometry(ctypes.byref(params), ctypes.byref(geom), ctypes.c_void_p(phi.data_ptr()),
+                                  ctypes.c_void_p(_stream_handle(stream))), "fsl_fill_geometry")
+
+
+_STORAGE_DTYPE = {F32: torch.float32, F16_OFS: torch.float16, BF16_OFS: torch.bfloat16}
+
+
+class Sim:
+    """One FSLBM context with its caller-owned device buffers (torch tensors)."""
+
+    def __init__(self, params: Params, phi0=None, obstacle=None, device="cuda", stream=None, phi_on_device=False):
+        self.p = params
+        self.shape = (params.nz, params.ny, params.nx)
+        self.N = params.nx * params.ny * params.nz
+        self.device = torch.device(device)
+        self.stream = stream
+        dt = _STORAGE_DTYPE[params.storage]
+        Np = (self.N + 3) // 4 * 4
+        self.f = [torch.empty((Q,) + self.shape, dtype=dt, device=self.device) for _ in range(2)]
+        self.flags = [torch.zeros(Np, dtype=torch.uint8, device=self.device) for _ in range(2)]
+        self.mass = torch.zeros(self.shape, dtype=torch.float32, device=self.device)
+        self.phi = torch.zeros(self.shape, dtype=torch.float32, device=self.device)
+        self.kappa = torch.zeros(self.shape, dtype=torch.float32, device=self.device)
+        ws = lib().fsl_workspace_size(ctypes.byref(params))
+        if ws == 0:
+            raise FslError("fsl_workspace_size: invalid parameters")
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        self.fields = Fields()
+        self.fields.f[0], self.fields.f[1] = self.f[0].data_ptr(), self.f[1].data_ptr()
+        self.fields.flags[0], self.fields.flags[1] = self.flags[0].data_ptr(), self.flags[1].data_ptr()
+        self.fields.mass, self.fields.phi = self.mass.data_ptr(), self.phi.data_ptr()
+        self.fields.kappa, self.fields.workspace = self.kappa.data_ptr(), self.workspace.data_ptr()
+        self._keep = []
+        phi_ptr, phi_where = None, WHERE_NONE
+        if phi0 is not None:
+            if isinstance(phi0, torch.Tensor) and phi0.is_cuda:
+                t = phi0.to(torch.float32).contiguous()
+                phi_ptr, phi_where = t.data_ptr(), WHERE_DEVICE
+            else:
+                t = torch.from_numpy(np.ascontiguousarray(phi0, dtype=np.float32)).pin_memory()
+                phi_ptr, phi_where = t.data_ptr(), WHERE_HOST
+            self._keep.append(t)
+        obs_ptr, obs_where = None, WHERE_NONE
+        if obstacle is not None:
+            if isinstance(obstacle, torch.Tensor) and obstacle.is_cuda:
+                t = obstacle.to(torch.uint8).contiguous()
+                obs_ptr, obs_where = t.data_ptr(), WHERE_DEVICE
+            else:
+                t = torch.from_numpy(np.ascontiguousarray(obstacle, dtype=np.uint8)).pin_memory()
+                obs_ptr, obs_where = t.data_ptr(), WHERE_HOST
+            self._keep.append(t)
+        ctx = ctypes.c_void_p()
+        check(lib().fsl_init(ctypes.byref(params), ctypes.byref(self.fields), phi_ptr, phi_where, obs_ptr, obs_where,
+                             ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(ctx)), "fsl_init")
+        self.ctx = ctx
+
+    # -- calls -----------------------------------------------------------------
+    def step(self, n: int = 1):
+        check(lib().fsl_step(self.ctx, int(n)), "fsl_step")
+
+    def step_profile(self) -> np.ndarray:
+        """One step launched kernel by kernel; device ms of normals, curvature,
+        stream-collide, conversion, finalize."""
+        out = (ctypes.c_float * 5)()
+        check(lib().fsl_step_profile(self.ctx, out), "fsl_step_profile")
+        return np.array(list(out), dtype=np.float64)
+
+    def curvature(self, model: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = self.kappa if out is None else out
+        check(lib().fsl_curvature(self.ctx, int(model), ctypes.c_void_p(out.data_ptr())), "fsl_curvature")
+        return out
+
+    def mass_total(self):
+        m, lost = ctypes.c_double(), ctypes.c_double()
+        check(lib().fsl_mass(self.ctx, ctypes.byref(m), ctypes.byref(lost)), "fsl_mass")
+        return m.value, lost.value
+
+    def stats(self) -> np.ndarray:
+        out = (ctypes.c_int64 * 8)()
+        check(lib().fsl_stats(self.ctx, out), "fsl_stats")
+        return np.array(list(out), dtype=np.int64)
+
+    def status(self) -> int:
+        return lib().fsl_status(self.ctx)
+
+    @property
+    def parity(self) -> int:
+        return lib().fsl_parity(self.ctx)
+
+    def refresh(self):
+        check(lib().fsl_refresh(self.ctx), "fsl_refresh")
+
+    # -- state access (host copies, for checks) ------------------------------------
+    def f_current(self) -> torch.Tensor:
+        return self.f[self.parity]
+
+    def flags_current(self) -> torch.Tensor:
+        return self.flags[self.parity][: self.N].view(self.shape)
+
+    def pdfs_float(self) -> torch.Tensor:
+        """Current PDFs decoded to float32 (16-bit offsets: f = w_q + v 2^-shift)."""
+        f = self.f_current()
+        if self.p.storage == F32:
+            return f
+        w = torch.tensor([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12, device=f.device).view(Q, 1, 1, 1)
+        return f.float() * (2.0 ** -self.p.storage_shift) + w
+
+    def set_state(self, f, flags, mass, phi):
+        """Write a state (host arrays) into the current buffers and refresh."""
+        p = self.parity
+        dt = _STORAGE_DTYPE[self.p.storage]
+        fx = torch.as_tensor(np.ascontiguousarray(f, dtype=np.float32))
+        if self.p.storage != F32:
+            w = torch.tensor([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12).view(Q, 1, 1, 1)
+            fx = (fx - w) * (2.0 ** self.p.storage_shift)
+        self.f[p].copy_(fx.to(dt))
+        fl = torch.as_tensor(np.ascontiguousarray(flags, dtype=np.uint8)).reshape(-1)
+        self.flags[p][: self.N].copy_(fl)
+        self.mass.copy_(torch.as_tensor(np.ascontiguousarray(mass, dtype=np.float32)))
+        self.phi.copy_(torch.as_tensor(np.ascontiguousarray(phi, dtype=np.float32)))
+        torch.cuda.synchronize(self.device)
+        self.refresh()
+
+    def host_state(self) -> dict:
+        torch.cuda.synchronize(self.device)
+        return dict(f=self.pdfs_float().double().cpu().numpy(), flags=self.flags_current().cpu().numpy(),
+                    mass=self.mass.double().cpu().numpy(), phi=self.phi.double().cpu().numpy(),
+                    kappa=self.kappa.double().cpu().numpy())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().fsl_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
