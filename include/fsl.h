@@ -79,7 +79,7 @@ typedef struct fsl_params {
     int32_t curv_model;     /* model used inside fsl_step */
     int32_t storage;        /* fsl_storage of the PDF buffers */
     int32_t storage_shift;  /* power-of-two scale of 16-bit offsets (e.g. 8) */
-    int32_t plic_iters;     /* bisection steps of the PLIC offset (e.g. 30) */
+    int32_t plic_iters;     /* Newton steps of the PLIC offset in its cubic branch (e.g. 4) */
     double tau;             /* relaxation time, nu = (tau - 1/2)/3; > 1/2 */
     double magic;           /* TRT Lambda = (tau - 1/2)(tau_odd - 1/2), e.g. 3/16 */
     double sigma;           /* surface tension */
@@ -93,7 +93,8 @@ typedef struct fsl_params {
 /* Caller-owned device buffers (all 256-byte aligned). */
 typedef struct fsl_fields {
     void *f[2];          /* 19*N PDFs each, element type per params.storage */
-    uint8_t *flags[2];   /* N bytes rounded up to a multiple of 4, each */
+    uint8_t *flags[2];   /* N bytes rounded up to a multiple of 4, each; flags[0]
+                            holds the cell types, flags[1] is scratch */
     float *mass;         /* N */
     float *phi;          /* N */
     float *kappa;        /* N */
@@ -132,13 +133,14 @@ int fsl_fill_geometry(const fsl_params *params, const fsl_geometry *geom, float 
  *   obstacle   N bytes, nonzero = obstacle cell, host or device, or FSL_NONE;
  * then types from phi (phi <= 0 gas, >= 1 liquid, else interface; every
  * liquid cell with a gas neighbour becomes interface), f = w_q, m = phi, and
- * the interface list.  fields->f[0] / flags[0] hold the state afterwards.
+ * the interface list.  fields->f[0] and flags[0] hold the state afterwards.
  * Asynchronous on `stream` (a cudaStream_t, or NULL for the default stream). */
 int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *phi0, int phi0_where,
              const uint8_t *obstacle, int obstacle_where, void *stream, struct fsl_ctx **out);
 
-/* The caller wrote a state directly into f[parity], flags[parity] (type bits),
- * mass and phi: recompute the near-obstacle bits and the interface list.
+/* The caller wrote a state directly into f[parity], flags[0] (type bits),
+ * mass and phi: recompute the near-obstacle bits, the interface list and the
+ * active row segments.
  * Asynchronous. */
 int fsl_refresh(struct fsl_ctx *ctx);
 
@@ -177,7 +179,7 @@ int fsl_stats(struct fsl_ctx *ctx, int64_t counts_out[8]);
  * conversion, finalize.  For profiling.  Synchronising. */
 int fsl_step_profile(struct fsl_ctx *ctx, float ms_out[5]);
 
-/* Which buffer (0 or 1) of fields->f / flags holds the current state. */
+/* Which buffer (0 or 1) of fields->f holds the current PDFs. */
 int fsl_parity(const struct fsl_ctx *ctx);
 
 /* Sticky device status (FSL_OK or an error code).  Synchronising. */

@@ -29,9 +29,11 @@ constexpr size_t ALIGN = 256;
 size_t up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t normal, rho, excess, iflist, fill, empty, newgas, liq2if, counts, lost, status, partial, stats, mass_out,
-        total;
+    size_t normal, rho, excess, iflist0, iflist1, fill, empty, newgas, liq2if, slow, seg_active, seg_list, counts,
+        lost, status, partial, stats, mass_out, total;
 };
+
+size_t nseg_of(const fsl_params &p) { return (size_t)((p.nx + SEG - 1) / SEG) * p.ny * p.nz; }
 
 Layout layout(const fsl_params &p) {
     const size_t N = (size_t)p.nx * p.ny * p.nz;
@@ -40,11 +42,15 @@ Layout layout(const fsl_params &p) {
     L.normal = o; o += up(N * sizeof(float4));
     L.rho = o; o += up(N * sizeof(float));
     L.excess = o; o += up(N * sizeof(float));
-    L.iflist = o; o += up(N * sizeof(int));
+    L.iflist0 = o; o += up(N * sizeof(int));
+    L.iflist1 = o; o += up(N * sizeof(int));
     L.fill = o; o += up(N * sizeof(int));
     L.empty = o; o += up(N * sizeof(int));
     L.newgas = o; o += up(N * sizeof(int));
     L.liq2if = o; o += up(N * sizeof(int));
+    L.slow = o; o += up(N * sizeof(int));
+    L.seg_active = o; o += up(nseg_of(p));
+    L.seg_list = o; o += up(nseg_of(p) * sizeof(int));
     L.counts = o; o += up(C_NCOUNT * sizeof(int));
     L.lost = o; o += up(sizeof(double));
     L.status = o; o += up(sizeof(int));
@@ -90,11 +96,17 @@ Dev make_dev(const fsl_params &p, const fsl_fields &f) {
     d.normal = reinterpret_cast<float4 *>(ws + L.normal);
     d.rho = reinterpret_cast<float *>(ws + L.rho);
     d.excess = reinterpret_cast<float *>(ws + L.excess);
-    d.iflist = reinterpret_cast<int *>(ws + L.iflist);
+    d.iflist = reinterpret_cast<int *>(ws + L.iflist0);
+    d.iflist_next = reinterpret_cast<int *>(ws + L.iflist1);
+    d.seg_active = reinterpret_cast<uint8_t *>(ws + L.seg_active);
+    d.seg_list = reinterpret_cast<int *>(ws + L.seg_list);
+    d.nsegx = (p.nx + SEG - 1) / SEG;
+    d.nseg = (int)nseg_of(p);
     d.fill = reinterpret_cast<int *>(ws + L.fill);
     d.empty = reinterpret_cast<int *>(ws + L.empty);
     d.newgas = reinterpret_cast<int *>(ws + L.newgas);
     d.liq2if = reinterpret_cast<int *>(ws + L.liq2if);
+    d.slow = reinterpret_cast<int *>(ws + L.slow);
     d.counts = reinterpret_cast<int *>(ws + L.counts);
     d.lost = reinterpret_cast<double *>(ws + L.lost);
     d.status = reinterpret_cast<int *>(ws + L.status);
@@ -120,12 +132,20 @@ Dev make_dev(const fsl_params &p, const fsl_fields &f) {
     return d;
 }
 
+// Parity p: PDFs f[p] -> f[1-p], interface list p -> 1-p.  The cell types
+// live in fields.flags[0] and are updated in place; fields.flags[1] is scratch.
 Dev dev_for(const fsl_ctx *c, int parity) {
     Dev d = c->base;
+    const Layout L = layout(c->p);
+    char *ws = static_cast<char *>(c->fields.workspace);
+    int *lists[2] = {reinterpret_cast<int *>(ws + L.iflist0), reinterpret_cast<int *>(ws + L.iflist1)};
     d.fsrc = c->fields.f[parity];
     d.fdst = c->fields.f[parity ^ 1];
-    d.flags = c->fields.flags[parity];
-    d.flags_next = c->fields.flags[parity ^ 1];
+    d.flags = c->fields.flags[0];
+    d.iflist = lists[parity];
+    d.iflist_next = lists[parity ^ 1];
+    d.cif = C_IF0 + parity;
+    d.cif_next = C_IF0 + (parity ^ 1);
     return d;
 }
 
@@ -146,7 +166,8 @@ void enqueue_curvature(const Dev &d, int model, float *kappa_out, cudaStream_t s
 int enqueue_step(const fsl_ctx *c, int parity, cudaStream_t s) {
     const Dev d = dev_for(c, parity);
     enqueue_curvature(d, c->p.curv_model, d.kappa, s);
-    CK(cudaMemsetAsync(d.counts, 0, C_NCOUNT * sizeof(int), s));
+    CK(cudaMemsetAsync(d.counts + C_FILL, 0, 4 * sizeof(int), s));  // fill, empty, newgas, liq2if
+    CK(cudaMemsetAsync(d.counts + d.cif_next, 0, sizeof(int), s));
     launch_stream_collide(d, s);
     launch_convert(d, s);
     launch_finalize(d, s);
@@ -219,13 +240,13 @@ int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *ph
         if (cudaMemsetAsync(c->base.status, 0, sizeof(int), s) != cudaSuccess) break;
         if (cudaMemsetAsync(c->base.normal, 0, N * sizeof(float4), s) != cudaSuccess) break;
         if (cudaMemsetAsync(fields->kappa, 0, N * sizeof(float), s) != cudaSuccess) break;
-        Dev d = dev_for(c, 1);  // fdst = f[0], flags_next = flags[0]
+        if (cudaMemsetAsync(c->base.seg_active, 0, c->base.nseg, s) != cudaSuccess) break;
+        Dev d = dev_for(c, 1);  // fdst = f[0]
         launch_init_types(d, obs, fields->flags[1], s);
-        Dev d0 = c->base;
+        Dev d0 = dev_for(c, 0);
         d0.fdst = fields->f[0];
-        d0.flags = fields->flags[0];
-        d0.flags_next = fields->flags[0];
         launch_init_state(d0, fields->flags[1], s);
+        launch_seg_compact(d0, s);
         if (cudaGetLastError() != cudaSuccess) break;
         c->parity = 0;
         rc = FSL_OK;
@@ -241,9 +262,10 @@ int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *ph
 int fsl_refresh(fsl_ctx *c) {
     if (!c) return FSL_EINVAL;
     Dev d = dev_for(c, c->parity);
-    d.flags_next = d.flags;
     CK(cudaMemsetAsync(d.counts, 0, C_NCOUNT * sizeof(int), c->stream));
+    CK(cudaMemsetAsync(d.seg_active, 0, d.nseg, c->stream));
     launch_refresh(d, c->stream);
+    launch_seg_compact(d, c->stream);
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
 }
 
@@ -275,7 +297,8 @@ int fsl_step_profile(fsl_ctx *c, float ms_out[5]) {
         if (c->p.curv_model == FSL_CURV_LSQR) launch_lsqr(d, d.kappa, s);
         else if (c->p.curv_model == FSL_CURV_FD) launch_fd(d, d.kappa, s);
         else launch_zero_kappa(d, d.kappa, s);
-        if (cudaMemsetAsync(d.counts, 0, C_NCOUNT * sizeof(int), s) != cudaSuccess) break;
+        if (cudaMemsetAsync(d.counts + C_FILL, 0, 4 * sizeof(int), s) != cudaSuccess) break;
+        if (cudaMemsetAsync(d.counts + d.cif_next, 0, sizeof(int), s) != cudaSuccess) break;
         if (cudaEventRecord(ev[2], s) != cudaSuccess) break;
         launch_stream_collide(d, s);
         if (cudaEventRecord(ev[3], s) != cudaSuccess) break;
@@ -322,7 +345,7 @@ int fsl_stats(fsl_ctx *c, int64_t counts_out[8]) {
     CK(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < 6; ++k) counts_out[k] = c->host_stats[k];
     counts_out[6] = cnt[C_FP64];
-    counts_out[7] = cnt[C_IF];
+    counts_out[7] = cnt[C_IF0 + c->parity];
     return FSL_OK;
 }
 

@@ -45,8 +45,14 @@ enum : uint8_t {
     B_NEW = 128,   // gas or liquid cell that becomes interface this step
 };
 
-// device counters in the workspace
-enum { C_IF = 0, C_FILL = 1, C_EMPTY = 2, C_NEWGAS = 3, C_LIQ2IF = 4, C_FP64 = 5, C_NCOUNT = 16 };
+// device counters in the workspace: interface-list lengths of the two list
+// buffers, conversion lists, FP64 LSQR re-solves, active segments
+enum { C_IF0 = 0, C_IF1 = 1, C_FILL = 2, C_EMPTY = 3, C_NEWGAS = 4, C_LIQ2IF = 5, C_FP64 = 6, C_SEG = 7, C_SLOW = 8,
+       C_NCOUNT = 16 };
+
+// the grid is walked in x-row segments of SEG cells (one warp each); a
+// segment is active while it holds a liquid or interface cell
+constexpr int SEG = 32;
 
 // status word values (sticky; first error wins)
 __device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
@@ -57,11 +63,17 @@ struct Dev {
     long long N;
     const void *fsrc;  // post-collision PDFs at t
     void *fdst;        // post-collision PDFs at t+1
-    uint8_t *flags;      // types at t (+ transient bits during a step)
-    uint8_t *flags_next; // types at t+1
+    uint8_t *flags;    // cell types (+ transient bits during a step), updated in place
     float *mass, *phi, *kappa, *rho, *excess;
     float4 *normal;
-    int *iflist, *fill, *empty, *newgas, *liq2if;
+    int *iflist;       // interface cells at t
+    int *iflist_next;  // interface cells at t+1 (built by the step)
+    int cif, cif_next; // their counters
+    int *fill, *empty, *newgas, *liq2if;
+    int *slow;         // interface cells whose LSQR fit takes the general path
+    uint8_t *seg_active;
+    int *seg_list;
+    int nsegx, nseg;
     int *counts;
     double *lost;
     int *status;
@@ -123,19 +135,19 @@ struct Store<FSL_BF16_OFS> {
 // ---- indexing ----------------------------------------------------------------
 __device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
-__device__ __forceinline__ long long cell_index(const Dev &d, int x, int y, int z) {
-    return (long long)x + (long long)d.nx * ((long long)y + (long long)d.ny * z);
-}
+// cell indices fit in int32 (N < 2^31 is checked at init); only q*N offsets
+// into the PDF arrays need 64 bits
+__device__ __forceinline__ int cell_index(const Dev &d, int x, int y, int z) { return x + d.nx * (y + d.ny * z); }
 
-__device__ __forceinline__ long long nbr_index(const Dev &d, int x, int y, int z, int dx, int dy, int dz) {
+__device__ __forceinline__ int nbr_index(const Dev &d, int x, int y, int z, int dx, int dy, int dz) {
     return cell_index(d, wrap(x + dx, d.nx), wrap(y + dy, d.ny), wrap(z + dz, d.nz));
 }
 
-__device__ __forceinline__ void cell_coords(const Dev &d, long long i, int &x, int &y, int &z) {
-    long long row = i / d.nx;
-    x = (int)(i - row * d.nx);
-    z = (int)(row / d.ny);
-    y = (int)(row - (long long)z * d.ny);
+__device__ __forceinline__ void cell_coords(const Dev &d, int i, int &x, int &y, int &z) {
+    const int row = i / d.nx;
+    x = i - row * d.nx;
+    z = row / d.ny;
+    y = row - z * d.ny;
 }
 
 // Warp-aggregated append of `value` to `list` when `pred` holds.  Every lane of
@@ -151,11 +163,27 @@ __device__ __forceinline__ void warp_append(int *list, int *count, bool pred, in
     if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = value;
 }
 
+// Loop of a list kernel with a warp-uniform trip count, so that warp_append can
+// be used inside: calls body(k, valid) for k = base + lane.
+template <typename Body>
+__device__ __forceinline__ void warp_uniform_loop(int n, Body body) {
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int base = gwarp * 32; base < n; base += nwarps * 32) body(base + lane, base + lane < n);
+}
+
+__device__ __forceinline__ int seg_of(const Dev &d, int i) {
+    const int row = i / d.nx;
+    return (i - row * d.nx) / SEG + d.nsegx * row;
+}
+
 // ---- launch wrappers (defined in the .cu files) -------------------------------
 void launch_fill_geometry(const fsl_params &p, const fsl_geometry &g, float *phi, cudaStream_t s);
 void launch_init_types(const Dev &d, const uint8_t *obstacle, uint8_t *tmp, cudaStream_t s);
 void launch_init_state(const Dev &d, const uint8_t *tmp, cudaStream_t s);
 void launch_refresh(const Dev &d, cudaStream_t s);
+void launch_seg_compact(const Dev &d, cudaStream_t s);
 void launch_stats(const Dev &d, cudaStream_t s);
 void launch_mass(const Dev &d, double *out, cudaStream_t s);
 void launch_stream_collide(const Dev &d, cudaStream_t s);
@@ -167,6 +195,7 @@ void launch_fd(const Dev &d, float *kappa_out, cudaStream_t s);
 void launch_zero_kappa(const Dev &d, float *kappa_out, cudaStream_t s);
 
 int max_partials();
-int list_grid(const Dev &d);
+// blocks of `block` threads of `kernel` that are resident on the whole GPU at once
+int resident_grid(const void *kernel, int block, size_t smem = 0);
 
 }  // namespace fslk

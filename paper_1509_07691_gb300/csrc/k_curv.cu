@@ -49,7 +49,7 @@ __device__ __forceinline__ float phi_ext(const Dev &d, int x, int y, int z) {
     x = wrap(x, d.nx);
     y = wrap(y, d.ny);
     z = wrap(z, d.nz);
-    const long long i = cell_index(d, x, y, z);
+    const int i = cell_index(d, x, y, z);
     if (!(d.flags[i] & T_OBS)) return d.phi[i];
     return reflect(d, x, y, z, [&](int a, int b, int c) { return d.phi[nbr_index(d, a, b, c, 0, 0, 0)]; });
 }
@@ -92,6 +92,52 @@ __device__ __forceinline__ float plic_vol(float m1, float m2, float m3, float al
     return al <= 0.5f ? plic_vol_half(m1, m2, m3, al) : 1.0f - plic_vol_half(m1, m2, m3, 1.0f - al);
 }
 
+// dV/dal of plic_vol_half, branch by branch
+__device__ __forceinline__ float plic_dvol_half(float m1, float m2, float m3, float al) {
+    if (al < m1) return al * al / (2.0f * m1 * m2 * m3);
+    if (al < m2) return (2.0f * al - m1) / (2.0f * m2 * m3);
+    if (al >= m1 + m2) return 1.0f / m3;
+    const float e2 = al - m2;
+    float t = 6.0f * al - 3.0f * m1 - 3.0f * e2 * (e2 / m1);
+    if (al >= m3) {
+        const float e3 = al - m3;
+        t -= 3.0f * e3 * (e3 / m1);
+    }
+    return t / (6.0f * m2 * m3);
+}
+
+// Inverse of plic_vol: al with V(al) = phi.  By symmetry only V <= 1/2 is
+// solved.  The branch is found from V at the break points m1, m2 and
+// min(m3, m1 + m2); the corner tetrahedron (cube root), the two-plane wedge
+// (quadratic) and the four-edge slab (linear) are solved in closed form, the
+// remaining cubic by Newton from the secant between its break points.
+__device__ float plic_alpha(float m1, float m2, float m3, float phi, int iters) {
+    const bool mirror = phi > 0.5f;
+    const float v = mirror ? 1.0f - phi : phi;
+    const float V1 = m1 > 0.f ? m1 * m1 / (6.0f * m2 * m3) : 0.f;
+    const float V2 = m2 > 0.f ? (3.0f * m2 * m2 - 3.0f * m2 * m1 + m1 * m1) / (6.0f * m2 * m3) : 0.f;
+    const float a3 = fminf(m3, m1 + m2);
+    const float V3 = plic_vol_half(m1, m2, m3, a3);
+    float al;
+    if (v < V1) {
+        al = cbrtf(6.0f * m1 * m2 * m3 * v);
+    } else if (v < V2) {
+        al = 0.5f * m1 + sqrtf(fmaxf(72.0f * m2 * m3 * v - 3.0f * m1 * m1, 0.f)) * (1.0f / 6.0f);
+    } else if (v >= V3 && m3 >= m1 + m2) {
+        al = m3 * v + 0.5f * (m1 + m2);
+    } else {
+        float lo, hi, vlo, vhi;
+        if (v < V3) { lo = m2; hi = a3; vlo = V2; vhi = V3; }
+        else { lo = a3; hi = 0.5f; vlo = V3; vhi = 0.5f; }
+        al = vhi > vlo ? lo + (hi - lo) * (v - vlo) / (vhi - vlo) : lo;
+        for (int it = 0; it < iters; ++it) {
+            const float g = plic_vol_half(m1, m2, m3, al) - v;
+            al = fminf(fmaxf(al - g / plic_dvol_half(m1, m2, m3, al), lo), hi);
+        }
+    }
+    return mirror ? 1.0f - al : al;
+}
+
 // Offset a of the plane {y.n = a} through the cell [-1/2,1/2]^3 whose liquid
 // side {y.n >= a} holds volume phi.  With m = |n| / sum|n| and
 // al = 1/2 - a / sum|n| the liquid part is {z : m.z <= al} of the unit cube.
@@ -100,23 +146,16 @@ __device__ float plic_offset(float nx, float ny, float nz, float phi, int iters)
     const float M = a1 + a2 + a3;
     if (phi <= 0.f) return 0.5f * M;
     if (phi >= 1.f) return -0.5f * M;
-    // sort
     float t;
     if (a1 > a2) { t = a1; a1 = a2; a2 = t; }
     if (a2 > a3) { t = a2; a2 = a3; a3 = t; }
     if (a1 > a2) { t = a1; a1 = a2; a2 = t; }
     const float m1 = a1 / M, m2 = a2 / M, m3 = 1.0f - m1 - m2;
-    float lo = 0.f, hi = 1.f;
-    for (int it = 0; it < iters; ++it) {
-        const float mid = 0.5f * (lo + hi);
-        if (plic_vol(m1, m2, m3, mid) < phi) lo = mid;
-        else hi = mid;
-    }
-    return M * (0.5f - 0.5f * (lo + hi));
+    return M * (0.5f - plic_alpha(m1, m2, m3, phi, iters));
 }
 
 __global__ void __launch_bounds__(LIST_THREADS) k_normals(Dev d) {
-    const int n = __ldcg(d.counts + C_IF);
+    const int n = __ldcg(d.counts + d.cif);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = d.iflist[k];
         int x, y, z;
@@ -296,79 +335,92 @@ __device__ float lsqr_cell(const Dev &d, int i, int x, int y, int z, float &cond
     red.init();
     const int kf = cons ? 3 : 5, kr = cons ? 1 : 3;
     int m = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                if (dx == 0 && dy == 0 && dz == 0) continue;
-                const long long j = nbr_index(d, x, y, z, dx, dy, dz);
-                const uint8_t fj = d.flags[j];
-                if (!(fj & T_IF)) continue;
-                const float4 q4 = d.normal[j];
-                if (q4.x == 0.f && q4.y == 0.f && q4.z == 0.f) continue;
-                const T nj[3] = {T(q4.x), T(q4.y), T(q4.z)};
-                const T aj = T(q4.w);
-                const T o[3] = {T(dx), T(dy), T(dz)};
-                const T dv[3] = {o[0] + aj * nj[0] - p[0], o[1] + aj * nj[1] - p[1], o[2] + aj * nj[2] - p[2]};
-                const T u = dot3(dv, tu), v = dot3(dv, tv), f = dot3(dv, n);
-                if (!cons) {
-                    T rf[5] = {u * u, v * v, u * v, u, v};
-                    T rr[3] = {u * u + v * v, u, v};
-                    full.add(rf, f, kf);
-                    red.add(rr, f, kr);
-                } else {
-                    const T rhs = f - gu * u - gv * v;
-                    T rf[5] = {u * u - T(2) * uc * u, v * v - T(2) * vc * v, u * v - vc * u - uc * v, T(0), T(0)};
-                    T rr[3] = {u * u + v * v - T(2) * uc * u - T(2) * vc * v, T(0), T(0)};
-                    full.add(rf, rhs, kf);
-                    red.add(rr, rhs, kr);
-                }
-                ++m;
-                if (fj & B_NEAR) {
-                    T pc[3], mh[3];
-                    int xj, yj, zj;
-                    cell_coords(d, j, xj, yj, zj);
-                    if (!contact<T>(d, xj, yj, zj, o, nj, aj, pc, mh)) continue;
-                    const T mn = dot3(mh, n);
-                    if (fabs(mn) < T(1e-6)) continue;
-                    const T dc[3] = {pc[0] - p[0], pc[1] - p[1], pc[2] - p[2]};
-                    const T uj = dot3(dc, tu), vj = dot3(dc, tv);
-                    const T g1 = -dot3(mh, tu) / mn, g2 = -dot3(mh, tv) / mn;
-                    if (!cons) {
-                        T r1[5] = {T(2) * uj, T(0), vj, T(1), T(0)};
-                        T r2[5] = {T(0), T(2) * vj, uj, T(0), T(1)};
-                        T s1[3] = {T(2) * uj, T(1), T(0)};
-                        T s2[3] = {T(2) * vj, T(0), T(1)};
-                        full.add(r1, g1, kf);
-                        full.add(r2, g2, kf);
-                        red.add(s1, g1, kr);
-                        red.add(s2, g2, kr);
-                    } else {
-                        T r1[5] = {T(2) * (uj - uc), T(0), vj - vc, T(0), T(0)};
-                        T r2[5] = {T(0), T(2) * (vj - vc), uj - uc, T(0), T(0)};
-                        T s1[3] = {T(2) * (uj - uc), T(0), T(0)};
-                        T s2[3] = {T(2) * (vj - vc), T(0), T(0)};
-                        full.add(r1, g1 - gu, kf);
-                        full.add(r2, g2 - gv, kf);
-                        red.add(s1, g1 - gu, kr);
-                        red.add(s2, g2 - gv, kr);
-                    }
-                    m += 2;
-                }
+    const int xs[3] = {x == 0 ? d.nx - 1 : x - 1, x, x == d.nx - 1 ? 0 : x + 1};
+    const int ys[3] = {y == 0 ? d.ny - 1 : y - 1, y, y == d.ny - 1 ? 0 : y + 1};
+    const int zs[3] = {z == 0 ? d.nz - 1 : z - 1, z, z == d.nz - 1 ? 0 : z + 1};
+    for (int dz = -1; dz <= 1; ++dz) {
+        // one z-plane of the neighbourhood: all nine flags and normals are
+        // loaded before any of them is used (independent loads in flight)
+        int jj[9];
+        uint8_t fjs[9];
+        float4 q4s[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) jj[t] = cell_index(d, xs[t % 3], ys[t / 3], zs[dz + 1]);
+#pragma unroll
+        for (int t = 0; t < 9; ++t) fjs[t] = d.flags[jj[t]];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) q4s[t] = d.normal[jj[t]];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int dx = t % 3 - 1, dy = t / 3 - 1;
+            if (dx == 0 && dy == 0 && dz == 0) continue;
+            const uint8_t fj = fjs[t];
+            if (!(fj & T_IF)) continue;
+            const float4 q4 = q4s[t];
+            if (q4.x == 0.f && q4.y == 0.f && q4.z == 0.f) continue;
+            const T nj[3] = {T(q4.x), T(q4.y), T(q4.z)};
+            const T aj = T(q4.w);
+            const T o[3] = {T(dx), T(dy), T(dz)};
+            const T dv[3] = {o[0] + aj * nj[0] - p[0], o[1] + aj * nj[1] - p[1], o[2] + aj * nj[2] - p[2]};
+            const T u = dot3(dv, tu), v = dot3(dv, tv), f = dot3(dv, n);
+            if (!cons) {
+                T rf[5] = {u * u, v * v, u * v, u, v};
+                T rr[3] = {u * u + v * v, u, v};
+                full.add(rf, f, kf);
+                red.add(rr, f, kr);
+            } else {
+                const T rhs = f - gu * u - gv * v;
+                T rf[5] = {u * u - T(2) * uc * u, v * v - T(2) * vc * v, u * v - vc * u - uc * v, T(0), T(0)};
+                T rr[3] = {u * u + v * v - T(2) * uc * u - T(2) * vc * v, T(0), T(0)};
+                full.add(rf, rhs, kf);
+                red.add(rr, rhs, kr);
             }
+            ++m;
+            if (fj & B_NEAR) {
+                T pc[3], mh[3];
+                if (!contact<T>(d, xs[dx + 1], ys[dy + 1], zs[dz + 1], o, nj, aj, pc, mh)) continue;
+                const T mn = dot3(mh, n);
+                if (fabs(mn) < T(1e-6)) continue;
+                const T dc[3] = {pc[0] - p[0], pc[1] - p[1], pc[2] - p[2]};
+                const T uj = dot3(dc, tu), vj = dot3(dc, tv);
+                const T g1 = -dot3(mh, tu) / mn, g2 = -dot3(mh, tv) / mn;
+                if (!cons) {
+                    T r1[5] = {T(2) * uj, T(0), vj, T(1), T(0)};
+                    T r2[5] = {T(0), T(2) * vj, uj, T(0), T(1)};
+                    T s1[3] = {T(2) * uj, T(1), T(0)};
+                    T s2[3] = {T(2) * vj, T(0), T(1)};
+                    full.add(r1, g1, kf);
+                    full.add(r2, g2, kf);
+                    red.add(s1, g1, kr);
+                    red.add(s2, g2, kr);
+                } else {
+                    T r1[5] = {T(2) * (uj - uc), T(0), vj - vc, T(0), T(0)};
+                    T r2[5] = {T(0), T(2) * (vj - vc), uj - uc, T(0), T(0)};
+                    T s1[3] = {T(2) * (uj - uc), T(0), T(0)};
+                    T s2[3] = {T(2) * (vj - vc), T(0), T(0)};
+                    full.add(r1, g1 - gu, kf);
+                    full.add(r2, g2 - gv, kf);
+                    red.add(s1, g1 - gu, kr);
+                    red.add(s2, g2 - gv, kr);
+                }
+                m += 2;
+            }
+        }
+    }
     T A = T(0), B = T(0), C = T(0), H = T(0), I = T(0);
     T cond = T(1);
-    T xs[5] = {T(0), T(0), T(0), T(0), T(0)};
+    T sol[5] = {T(0), T(0), T(0), T(0), T(0)};
     bool done = false;
-    if (m >= kf && full.solve(xs, kf, cond)) {
-        A = xs[0];
-        B = xs[1];
-        C = xs[2];
+    if (m >= kf && full.solve(sol, kf, cond)) {
+        A = sol[0];
+        B = sol[1];
+        C = sol[2];
         if (cons) {
             H = gu - T(2) * uc * A - vc * C;
             I = gv - T(2) * vc * B - uc * C;
         } else {
-            H = xs[3];
-            I = xs[4];
+            H = sol[3];
+            I = sol[4];
         }
         done = true;
     } else {
@@ -393,10 +445,93 @@ __device__ float lsqr_cell(const Dev &d, int i, int x, int y, int z, float &cond
     return (float)((A * (T(1) + I * I) + B * (T(1) + H * H) - C * H * I) / (g * sqrt(g)));
 }
 
-__global__ void __launch_bounds__(LIST_THREADS) k_lsqr(Dev d, float *kappa_out) {
-    const int n = __ldcg(d.counts + C_IF);
+// Fast path: FP32 fit of the full model for an interface cell with no
+// contact-line cell in its neighbourhood.  Returns false (cell left to the
+// general path) when a contact-line cell is present, when there are fewer
+// than five rows, or when R is rank deficient or ill conditioned.
+__device__ bool lsqr_fast(const Dev &d, int i, int x, int y, int z, float &kap) {
+    const float4 c4 = d.normal[i];
+    kap = 0.f;
+    if (c4.x == 0.f && c4.y == 0.f && c4.z == 0.f) return true;
+    if (d.flags[i] & B_NEAR) return false;
+    const float n[3] = {c4.x, c4.y, c4.z};
+    int k = 0;
+    if (fabsf(n[1]) < fabsf(n[0])) k = 1;
+    if (fabsf(n[2]) < fabsf(n[k])) k = 2;
+    float tu[3];
+    if (k == 0) { tu[0] = 0.f; tu[1] = -n[2]; tu[2] = n[1]; }
+    else if (k == 1) { tu[0] = n[2]; tu[1] = 0.f; tu[2] = -n[0]; }
+    else { tu[0] = -n[1]; tu[1] = n[0]; tu[2] = 0.f; }
+    const float tl = rsqrtf(dot3(tu, tu));
+    tu[0] *= tl;
+    tu[1] *= tl;
+    tu[2] *= tl;
+    const float tv[3] = {n[1] * tu[2] - n[2] * tu[1], n[2] * tu[0] - n[0] * tu[2], n[0] * tu[1] - n[1] * tu[0]};
+    const float p[3] = {c4.w * n[0], c4.w * n[1], c4.w * n[2]};
+    Givens<float, 5> full;
+    full.init();
+    int m = 0;
+    const int xs[3] = {x == 0 ? d.nx - 1 : x - 1, x, x == d.nx - 1 ? 0 : x + 1};
+    const int ys[3] = {y == 0 ? d.ny - 1 : y - 1, y, y == d.ny - 1 ? 0 : y + 1};
+    const int zs[3] = {z == 0 ? d.nz - 1 : z - 1, z, z == d.nz - 1 ? 0 : z + 1};
+#pragma unroll 1
+    for (int pz = 0; pz < 3; ++pz) {
+        int jj[9];
+        uint8_t fjs[9];
+        float4 q4s[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) jj[t] = cell_index(d, xs[t % 3], ys[t / 3], zs[pz]);
+#pragma unroll
+        for (int t = 0; t < 9; ++t) fjs[t] = d.flags[jj[t]];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) q4s[t] = d.normal[jj[t]];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            if (pz == 1 && t == 4) continue;
+            if (!(fjs[t] & T_IF)) continue;
+            if (fjs[t] & B_NEAR) return false;
+            const float4 q4 = q4s[t];
+            if (q4.x == 0.f && q4.y == 0.f && q4.z == 0.f) continue;
+            const float dv[3] = {(float)(t % 3 - 1) + q4.w * q4.x - p[0], (float)(t / 3 - 1) + q4.w * q4.y - p[1],
+                                 (float)(pz - 1) + q4.w * q4.z - p[2]};
+            const float u = dot3(dv, tu), v = dot3(dv, tv), f = dot3(dv, n);
+            float rf[5] = {u * u, v * v, u * v, u, v};
+            full.add(rf, f, 5);
+            ++m;
+        }
+    }
+    if (m < 5) return false;
+    float sol[5], cond;
+    if (!full.solve(sol, 5, cond) || cond > d.fp64_cond) return false;
+    const float A = sol[0], B = sol[1], C = sol[2], H = sol[3], I = sol[4];
+    const float g = 1.0f + H * H + I * I;
+    kap = (A * (1.0f + I * I) + B * (1.0f + H * H) - C * H * I) / (g * sqrtf(g));
+    return true;
+}
+
+__global__ void __launch_bounds__(LIST_THREADS) k_lsqr_fast(Dev d, float *kappa_out) {
+    const int n = __ldcg(d.counts + d.cif);
+    warp_uniform_loop(n, [&](int k, bool valid) {
+        bool defer = false;
+        int i = 0;
+        if (valid) {
+            i = d.iflist[k];
+            int x, y, z;
+            cell_coords(d, i, x, y, z);
+            float kap;
+            if (lsqr_fast(d, i, x, y, z, kap)) kappa_out[i] = kap;
+            else defer = true;
+        }
+        warp_append(d.slow, d.counts + C_SLOW, defer, i);
+    });
+}
+
+// General path: contact rows and centre constraint, isotropic fallback, FP64
+// re-solve when the FP32 R is ill conditioned
+__global__ void __launch_bounds__(LIST_THREADS) k_lsqr_slow(Dev d, float *kappa_out) {
+    const int n = __ldcg(d.counts + C_SLOW);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int i = d.iflist[k];
+        const int i = d.slow[k];
         int x, y, z;
         cell_coords(d, i, x, y, z);
         float cond;
@@ -490,7 +625,7 @@ __device__ void fd_normal(const Dev &d, int x, int y, int z, float n[3]) {
 }
 
 __global__ void __launch_bounds__(LIST_THREADS) k_fd(Dev d, float *kappa_out) {
-    const int n = __ldcg(d.counts + C_IF);
+    const int n = __ldcg(d.counts + d.cif);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = d.iflist[k];
         int x, y, z;
@@ -510,25 +645,28 @@ __global__ void __launch_bounds__(LIST_THREADS) k_fd(Dev d, float *kappa_out) {
 }
 
 __global__ void k_zero_kappa(Dev d, float *kappa_out) {
-    const int n = __ldcg(d.counts + C_IF);
+    const int n = __ldcg(d.counts + d.cif);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) kappa_out[d.iflist[k]] = 0.f;
 }
 
-int list_grid(const Dev &d) {
-    // enough blocks to fill the GPU; kernels stride over the device-side count
-    long long want = (d.N / 16 + LIST_THREADS - 1) / LIST_THREADS;
-    if (want < 152) want = 152;
-    if (want > 152 * 16) want = 152 * 16;
-    return (int)want;
+void launch_normals(const Dev &d, cudaStream_t s) {
+    static const int g = resident_grid((const void *)k_normals, LIST_THREADS);
+    k_normals<<<g, LIST_THREADS, 0, s>>>(d);
 }
-
-void launch_normals(const Dev &d, cudaStream_t s) { k_normals<<<list_grid(d), LIST_THREADS, 0, s>>>(d); }
 void launch_lsqr(const Dev &d, float *kappa_out, cudaStream_t s) {
-    k_lsqr<<<list_grid(d), LIST_THREADS, 0, s>>>(d, kappa_out);
+    static const int gf = resident_grid((const void *)k_lsqr_fast, LIST_THREADS);
+    static const int gs = resident_grid((const void *)k_lsqr_slow, LIST_THREADS);
+    cudaMemsetAsync(d.counts + C_SLOW, 0, sizeof(int), s);
+    k_lsqr_fast<<<gf, LIST_THREADS, 0, s>>>(d, kappa_out);
+    k_lsqr_slow<<<gs, LIST_THREADS, 0, s>>>(d, kappa_out);
 }
-void launch_fd(const Dev &d, float *kappa_out, cudaStream_t s) { k_fd<<<list_grid(d), LIST_THREADS, 0, s>>>(d, kappa_out); }
+void launch_fd(const Dev &d, float *kappa_out, cudaStream_t s) {
+    static const int g = resident_grid((const void *)k_fd, LIST_THREADS);
+    k_fd<<<g, LIST_THREADS, 0, s>>>(d, kappa_out);
+}
 void launch_zero_kappa(const Dev &d, float *kappa_out, cudaStream_t s) {
-    k_zero_kappa<<<list_grid(d), LIST_THREADS, 0, s>>>(d, kappa_out);
+    static const int g = resident_grid((const void *)k_zero_kappa, LIST_THREADS);
+    k_zero_kappa<<<g, LIST_THREADS, 0, s>>>(d, kappa_out);
 }
 
 }  // namespace fslk

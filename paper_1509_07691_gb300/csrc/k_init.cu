@@ -4,6 +4,14 @@
 
 namespace fslk {
 
+int resident_grid(const void *kernel, int block, size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, smem);
+    return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+}
+
 // ---- fill levels -------------------------------------------------------------
 // Inside tests in FP64 with explicitly rounded operations (no contraction),
 // evaluated in the same order as the sampling formula states, so that every
@@ -127,12 +135,13 @@ __global__ void __launch_bounds__(256) k_init_types(Dev d, const uint8_t *obstac
     tmp[i] = t;
 }
 
-// liquid cells touching gas become interface; phi, m = phi, f = w_q; interface list
+// liquid cells touching gas become interface; phi, m = phi, f = w_q; interface
+// list; active segments
 template <int S>
 __global__ void __launch_bounds__(256) k_init_state(Dev d, const uint8_t *tmp) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     const bool inb = x < d.nx;
-    const long long i = inb ? cell_index(d, x, y, z) : 0;
+    const int i = inb ? cell_index(d, x, y, z) : 0;
     bool is_if = false;
     if (inb) {
         uint8_t t = tmp[i];
@@ -151,8 +160,9 @@ __global__ void __launch_bounds__(256) k_init_state(Dev d, const uint8_t *tmp) {
         d.flags[i] = t | (obs_nbr ? B_NEAR : 0);
         for (int q = 0; q < Q; ++q) Store<S>::st(d.fdst, (long long)q * d.N + i, q, wq(q), d);
         is_if = t == T_IF;
+        if (t & (T_LIQ | T_IF)) d.seg_active[seg_of(d, i)] = 1;
     }
-    warp_append(d.iflist, d.counts + C_IF, is_if, (int)i);
+    warp_append(d.iflist, d.counts + d.cif, is_if, i);
 }
 
 void launch_init_types(const Dev &d, const uint8_t *obstacle, uint8_t *tmp, cudaStream_t s) {
@@ -168,20 +178,23 @@ void launch_init_state(const Dev &d, const uint8_t *tmp, cudaStream_t s) {
     }
 }
 
-// recompute near-obstacle bits and the interface list after the caller wrote a state
+// recompute near-obstacle bits, the interface list and the active segments
+// after the caller wrote a state (in place: only the near bit changes, and
+// readers look at type bits)
 __global__ void __launch_bounds__(256) k_refresh(Dev d) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     const bool inb = x < d.nx;
-    const long long i = inb ? cell_index(d, x, y, z) : 0;
+    const int i = inb ? cell_index(d, x, y, z) : 0;
     bool is_if = false;
     if (inb) {
         const uint8_t t = d.flags[i] & T_MASK;
         bool obs_nbr = false;
         for (int q = 1; q < Q; ++q) obs_nbr |= (d.flags[nbr_index(d, x, y, z, cx(q), cy(q), cz(q))] & T_OBS) != 0;
-        d.flags_next[i] = t | (obs_nbr ? B_NEAR : 0);
+        d.flags[i] = t | (obs_nbr ? B_NEAR : 0);
         is_if = t == T_IF;
+        if (t & (T_LIQ | T_IF)) d.seg_active[seg_of(d, i)] = 1;
     }
-    warp_append(d.iflist, d.counts + C_IF, is_if, (int)i);
+    warp_append(d.iflist, d.counts + d.cif, is_if, i);
 }
 
 void launch_refresh(const Dev &d, cudaStream_t s) {
@@ -193,7 +206,7 @@ void launch_refresh(const Dev &d, cudaStream_t s) {
 // stats[0..5]: liquid, interface, gas, obstacle, interface without liquid or gas
 // neighbour, liquid touching gas.  One atomic per block and counter.
 __global__ void __launch_bounds__(256) k_stats(Dev d) {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     int c[6] = {0, 0, 0, 0, 0, 0};
     if (i < d.N) {
         int x, y, z;

@@ -1,12 +1,17 @@
 // k_step.cu -- the FSLBM time step (Sec. II): fused pull stream-collide with the
 // free-boundary condition and mass exchange, conversion of interface cells
-// with excess-mass redistribution, and the final type update with the
-// interface list of the next step.
+// with excess-mass redistribution, and the update of the cell types, of the
+// interface list and of the active segments for the next step.
+//
+// Work decomposition: liquid cells are processed by k_sc_bulk over the active
+// x-row segments (coalesced SoA loads, one thread per cell); interface cells
+// by k_sc_iface over the interface list; everything after the collision only
+// touches list entries, so no pass sweeps the whole grid.
 #include "fsl_internal.cuh"
 
 namespace fslk {
 
-constexpr int SC_THREADS = 128;
+constexpr int LIST_BLOCK = 128;
 
 // BGK / TRT collision in place (Eq. lbe2).  TRT relaxes the even and odd
 // parts of each pair (q, opp q) with omega_e = 1/tau and omega_o = 1/tau_o.
@@ -47,44 +52,85 @@ __device__ __forceinline__ void collide(float f[Q], const Dev &d, float &rho_out
     }
 }
 
-// One thread per cell of an x row.  Gas and obstacle cells do nothing.
-// Liquid cells without obstacle neighbours take the plain pull path; the
-// others (interface, liquid next to a wall) resolve each link by the type of
-// its source cell x - c_q:
+// index of the source cell x - c_q of every direction
+__device__ __forceinline__ void sources(const Dev &d, int x, int y, int z, int src[Q]) {
+    const int xs[3] = {x == d.nx - 1 ? 0 : x + 1, x, x == 0 ? d.nx - 1 : x - 1};  // x - c for c = -1, 0, 1
+    const int ys[3] = {y == d.ny - 1 ? 0 : y + 1, y, y == 0 ? d.ny - 1 : y - 1};
+    const int zs[3] = {z == d.nz - 1 ? 0 : z + 1, z, z == 0 ? d.nz - 1 : z - 1};
+#pragma unroll
+    for (int q = 0; q < Q; ++q) src[q] = cell_index(d, xs[cx(q) + 1], ys[cy(q) + 1], zs[cz(q) + 1]);
+}
+
+// Liquid cells of the active segments: pull stream (Eq. lbe1) and collide.
+// One warp per 32-cell x-row segment, one thread per cell (coalesced SoA
+// loads and stores).  A liquid cell next to a wall takes bounce-back
+// f_q(x) = f'_qbar(x) on its obstacle links.  Interface cells are left to
+// k_sc_iface.  A segment without any liquid or interface cell is marked
+// inactive.
+template <int S, int COLL>
+__global__ void __launch_bounds__(256) k_sc_bulk(Dev d) {
+    using St = Store<S>;
+    const int nseg = __ldcg(d.counts + C_SEG);
+    const long long N = d.N;
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int k = gw; k < nseg; k += nw) {
+        const int s = d.seg_list[k];
+        const int row = s / d.nsegx;
+        const int x = (s - row * d.nsegx) * SEG + lane;
+        const int z = row / d.ny, y = row - z * d.ny;
+        const bool inb = x < d.nx;
+        const int i = inb ? cell_index(d, x, y, z) : 0;
+        const uint8_t fl = inb ? d.flags[i] : (uint8_t)T_GAS;
+        if (fl & T_LIQ) {
+            int src[Q];
+            sources(d, x, y, z, src);
+            float f[Q];
+            if (!(fl & B_NEAR)) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) f[q] = St::ld(d.fsrc, (long long)q * N + src[q], q, d);
+            } else {
+                f[0] = St::ld(d.fsrc, i, 0, d);
+#pragma unroll
+                for (int q = 1; q < Q; ++q) {
+                    const bool wall = (d.flags[src[q]] & T_OBS) != 0;
+                    f[q] = wall ? St::ld(d.fsrc, (long long)opp(q) * N + i, opp(q), d)
+                                : St::ld(d.fsrc, (long long)q * N + src[q], q, d);
+                }
+            }
+            float rho;
+            collide<COLL>(f, d, rho);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) St::st(d.fdst, (long long)q * N + i, q, f[q], d);
+        }
+        if (!__any_sync(0xffffffffu, (fl & (T_LIQ | T_IF)) != 0) && lane == 0) d.seg_active[s] = 0;
+    }
+}
+
+// Interface cells (list): each link by the type of its source cell x - c_q:
 //   fluid     f_q(x) = f'_q(x - c_q)                        (Eq. lbe1)
 //   gas       f_q(x) = feq_q + feq_qbar - f'_qbar(x)         (Eq. reconstruct)
 //             with rho_b = 3 p_g + 6 sigma kappa(x), u_b = u(x, t)
 //   obstacle  f_q(x) = f'_qbar(x) (bounce-back), or Eq. reconstruct at a
 //             contact-line cell when c_qbar . n_t < 0, n_t the interface normal
 //             projected into the wall (Fig. inhomo)
-// and interface cells add the mass exchange of Eqs. (advection1/2).
+// plus the mass exchange of Eqs. (advection1/2) and the conversion test.
 template <int S, int COLL>
-__global__ void __launch_bounds__(SC_THREADS) k_stream_collide(Dev d) {
+__global__ void __launch_bounds__(LIST_BLOCK) k_sc_iface(Dev d) {
     using St = Store<S>;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const bool inb = x < d.nx;
+    const int n = __ldcg(d.counts + d.cif);
     const long long N = d.N;
-    const long long i = inb ? cell_index(d, x, y, z) : 0;
-    const uint8_t fl = inb ? d.flags[i] : (uint8_t)T_GAS;
-    bool fill = false, empty = false;
-
-    if (fl & (T_LIQ | T_IF)) {
-        const int xs[3] = {x == d.nx - 1 ? 0 : x + 1, x, x == 0 ? d.nx - 1 : x - 1};  // x - c, c = -1,0,1
-        const int ys[3] = {y == d.ny - 1 ? 0 : y + 1, y, y == 0 ? d.ny - 1 : y - 1};
-        const int zs[3] = {z == d.nz - 1 ? 0 : z + 1, z, z == 0 ? d.nz - 1 : z - 1};
-        long long src[Q];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) src[q] = cell_index(d, xs[cx(q) + 1], ys[cy(q) + 1], zs[cz(q) + 1]);
-
-        float f[Q];
-        const bool is_if = (fl & T_IF) != 0;
-        float dm = 0.f;
-        if (!(fl & (T_IF | B_NEAR))) {
-#pragma unroll
-            for (int q = 0; q < Q; ++q) f[q] = St::ld(d.fsrc, (long long)q * N + src[q], q, d);
-        } else {
-            float fo[Q];
+    warp_uniform_loop(n, [&](int k, bool valid) {
+        bool fill = false, empty = false;
+        int i = 0;
+        if (valid) {
+            i = d.iflist[k];
+            int x, y, z;
+            cell_coords(d, i, x, y, z);
+            int src[Q];
+            sources(d, x, y, z, src);
+            const uint8_t fl = d.flags[i];
+            float fo[Q], f[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) fo[q] = St::ld(d.fsrc, (long long)q * N + i, q, d);
             uint8_t tq[Q];
@@ -112,9 +158,8 @@ __global__ void __launch_bounds__(SC_THREADS) k_stream_collide(Dev d) {
             }
             const float ux = jx / r0, uy = jy / r0, uz = jz / r0;
             const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
-            const float kap = is_if ? d.kappa[i] : 0.f;
-            const float rho_b = d.rho_gas + d.six_sigma * kap;
-            const bool corner = is_if && has_gas && has_obs;
+            const float rho_b = d.rho_gas + d.six_sigma * d.kappa[i];
+            const bool corner = has_gas && has_obs;
             float ntx = 0.f, nty = 0.f, ntz = 0.f;
             if (corner) {
                 const float4 n4 = d.normal[i];
@@ -127,7 +172,8 @@ __global__ void __launch_bounds__(SC_THREADS) k_stream_collide(Dev d) {
                 nty = n4.y - wn * wy;
                 ntz = n4.z - wn * wz;
             }
-            const float phix = is_if ? d.phi[i] : 0.f;
+            const float phix = d.phi[i];
+            float dm = 0.f;
             f[0] = fo[0];
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
@@ -138,10 +184,8 @@ __global__ void __launch_bounds__(SC_THREADS) k_stream_collide(Dev d) {
                 if (tq[q] & (T_LIQ | T_IF)) {
                     const float fin = St::ld(d.fsrc, (long long)q * N + src[q], q, d);
                     f[q] = fin;
-                    if (is_if) {
-                        const float k = (tq[q] & T_LIQ) ? 1.0f : 0.5f * (phix + d.phi[src[q]]);
-                        dm += k * (fin - fo[qb]);
-                    }
+                    const float kq = (tq[q] & T_LIQ) ? 1.0f : 0.5f * (phix + d.phi[src[q]]);
+                    dm += kq * (fin - fo[qb]);
                 } else if (tq[q] & T_OBS) {
                     const float outdir = -(cx(q) * ntx + cy(q) * nty + cz(q) * ntz);  // c_qbar . n_t
                     f[q] = (corner && outdir < 0.f) ? recon : fo[qb];
@@ -149,12 +193,10 @@ __global__ void __launch_bounds__(SC_THREADS) k_stream_collide(Dev d) {
                     f[q] = recon;
                 }
             }
-        }
-        float rho;
-        collide<COLL>(f, d, rho);
+            float rho;
+            collide<COLL>(f, d, rho);
 #pragma unroll
-        for (int q = 0; q < Q; ++q) St::st(d.fdst, (long long)q * N + i, q, f[q], d);
-        if (is_if) {
+            for (int q = 0; q < Q; ++q) St::st(d.fdst, (long long)q * N + i, q, f[q], d);
             const float m = d.mass[i] + dm;
             d.mass[i] = m;
             d.rho[i] = rho;
@@ -162,28 +204,23 @@ __global__ void __launch_bounds__(SC_THREADS) k_stream_collide(Dev d) {
             empty = !fill && (m < -d.eps * rho);
             if (fill || empty) d.flags[i] = fl | (fill ? B_TOLIQ : B_TOGAS);
         }
-    }
-    warp_append(d.fill, d.counts + C_FILL, fill, (int)i);
-    warp_append(d.empty, d.counts + C_EMPTY, empty, (int)i);
+        warp_append(d.fill, d.counts + C_FILL, fill, i);
+        warp_append(d.empty, d.counts + C_EMPTY, empty, i);
+    });
 }
 
-// Conversion (the paper cites Koerner et al. for it; readings):
+// ---- conversion (the paper cites Koerner et al. for it; readings) -------------
 //  A  an emptying cell with a filling D3Q19 neighbour stays interface;
 //  B  gas neighbours of filling cells and liquid neighbours of emptying cells
-//     become interface (deduplicated with an atomic OR on the flag word);
+//     become interface (deduplicated by an atomic OR on the flag word);
 //  C  new cells from gas get f = feq(mean rho, mean u) of their fluid
 //     neighbours and m = 0; cells from liquid keep f and get m = rho;
 //  D  the excess mass (m - rho of a filled cell, m of an emptied one) is
 //     divided equally among the neighbours that are interface after B; the
-//     receivers gather it in k_finalize.  No receiver: added to `lost`.
-// One block: conversions per step are few, and the phases need block barriers.
-template <int S>
-__global__ void __launch_bounds__(1024) k_convert(Dev d) {
-    using St = Store<S>;
-    const int nfill = __ldcg(d.counts + C_FILL), nempty = __ldcg(d.counts + C_EMPTY);
-    if (nfill + nempty == 0) return;
-    const long long N = d.N;
-    for (int k = threadIdx.x; k < nempty; k += blockDim.x) {
+//     receivers gather it in k_fin_a.  No receiver: added to `lost`.
+__global__ void __launch_bounds__(LIST_BLOCK) k_conv_a(Dev d) {
+    const int nempty = __ldcg(d.counts + C_EMPTY);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nempty; k += gridDim.x * blockDim.x) {
         const int i = d.empty[k];
         int x, y, z;
         cell_coords(d, i, x, y, z);
@@ -193,74 +230,108 @@ __global__ void __launch_bounds__(1024) k_convert(Dev d) {
                 break;
             }
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < nfill + nempty; k += blockDim.x) {
+}
+
+__global__ void __launch_bounds__(LIST_BLOCK) k_conv_b(Dev d) {
+    const int nfill = __ldcg(d.counts + C_FILL), nempty = __ldcg(d.counts + C_EMPTY);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nfill + nempty; k += gridDim.x * blockDim.x) {
         const bool isfill = k < nfill;
         const int i = isfill ? d.fill[k] : d.empty[k - nfill];
-        if (!isfill && !(__ldcg(d.flags + i) & B_TOGAS)) continue;
+        if (!isfill && !(d.flags[i] & B_TOGAS)) continue;
         int x, y, z;
         cell_coords(d, i, x, y, z);
         for (int q = 1; q < Q; ++q) {
-            const long long j = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
+            const int j = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
             const uint8_t fj = __ldcg(d.flags + j);
             if (isfill ? (fj & T_GAS) : (fj & T_LIQ)) {
-                unsigned *word = reinterpret_cast<unsigned *>(d.flags + (j & ~3LL));
-                const int sh = (int)(j & 3) * 8;
+                unsigned *word = reinterpret_cast<unsigned *>(d.flags + (j & ~3));
+                const int sh = (j & 3) * 8;
                 const unsigned old = atomicOr(word, (unsigned)B_NEW << sh);
                 if (!((old >> sh) & B_NEW)) {
-                    if (isfill) d.newgas[atomicAdd(d.counts + C_NEWGAS, 1)] = (int)j;
-                    else d.liq2if[atomicAdd(d.counts + C_LIQ2IF, 1)] = (int)j;
+                    if (isfill) {
+                        d.newgas[atomicAdd(d.counts + C_NEWGAS, 1)] = j;
+                        d.seg_active[seg_of(d, j)] = 1;
+                    } else {
+                        d.liq2if[atomicAdd(d.counts + C_LIQ2IF, 1)] = j;
+                    }
                 }
             }
         }
     }
-    __syncthreads();
+}
+
+// one warp per new cell; lane q (1..18) reads neighbour x + c_q
+template <int S>
+__global__ void __launch_bounds__(LIST_BLOCK) k_conv_c(Dev d) {
+    using St = Store<S>;
     const int ngas = __ldcg(d.counts + C_NEWGAS), nliq = __ldcg(d.counts + C_LIQ2IF);
-    for (int k = threadIdx.x; k < ngas + nliq; k += blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const long long N = d.N;
+    for (int k = gwarp; k < ngas + nliq; k += nwarps) {
         if (k < ngas) {
             const int j = d.newgas[k];
             int x, y, z;
             cell_coords(d, j, x, y, z);
-            float rs = 0.f, us[3] = {0.f, 0.f, 0.f};
-            int cnt = 0;
-            for (int q = 1; q < Q; ++q) {
-                const long long l = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
-                if (!(__ldcg(d.flags + l) & (T_LIQ | T_IF))) continue;
-                float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-                for (int p = 0; p < Q; ++p) {
-                    const float v = St::ldcg(d.fdst, (long long)p * N + l, p, d);
-                    r += v;
-                    jx += cx(p) * v;
-                    jy += cy(p) * v;
-                    jz += cz(p) * v;
+            float r = 0.f, ux = 0.f, uy = 0.f, uz = 0.f, c = 0.f;
+            if (lane >= 1 && lane < Q) {
+                const int q = lane;
+                const int l = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
+                if (d.flags[l] & (T_LIQ | T_IF)) {
+                    float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+                    for (int p = 0; p < Q; ++p) {
+                        const float v = St::ld(d.fdst, (long long)p * N + l, p, d);
+                        r += v;
+                        jx += cx(p) * v;
+                        jy += cy(p) * v;
+                        jz += cz(p) * v;
+                    }
+                    ux = jx / r;
+                    uy = jy / r;
+                    uz = jz / r;
+                    c = 1.f;
                 }
-                rs += r;
-                us[0] += jx / r;
-                us[1] += jy / r;
-                us[2] += jz / r;
-                ++cnt;
             }
-            const float rb = rs / cnt, ux = us[0] / cnt, uy = us[1] / cnt, uz = us[2] / cnt;
-            const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
-            for (int q = 0; q < Q; ++q) {
-                const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                r += __shfl_xor_sync(0xffffffffu, r, o);
+                ux += __shfl_xor_sync(0xffffffffu, ux, o);
+                uy += __shfl_xor_sync(0xffffffffu, uy, o);
+                uz += __shfl_xor_sync(0xffffffffu, uz, o);
+                c += __shfl_xor_sync(0xffffffffu, c, o);
+            }
+            const float rb = r / c, vx = ux / c, vy = uy / c, vz = uz / c;
+            if (lane < Q) {
+                const int q = lane;
+                const float uu = 1.5f * (vx * vx + vy * vy + vz * vz);
+                const float cu = cx(q) * vx + cy(q) * vy + cz(q) * vz;
                 St::st(d.fdst, (long long)q * N + j, q, wq(q) * rb * (1.0f + 3.0f * cu + 4.5f * cu * cu - uu), d);
             }
-            d.mass[j] = 0.f;
-            d.rho[j] = rb;
+            if (lane == 0) {
+                d.mass[j] = 0.f;
+                d.rho[j] = rb;
+            }
         } else {
             const int j = d.liq2if[k - ngas];
-            float r = 0.f;
-            for (int p = 0; p < Q; ++p) r += St::ldcg(d.fdst, (long long)p * N + j, p, d);
-            d.mass[j] = r;
-            d.rho[j] = r;
+            float r = lane < Q ? St::ld(d.fdst, (long long)lane * N + j, lane, d) : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+            if (lane == 0) {
+                d.mass[j] = r;
+                d.rho[j] = r;
+            }
         }
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < nfill + nempty; k += blockDim.x) {
+}
+
+__global__ void __launch_bounds__(LIST_BLOCK) k_conv_d(Dev d) {
+    const int nfill = __ldcg(d.counts + C_FILL), nempty = __ldcg(d.counts + C_EMPTY);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nfill + nempty; k += gridDim.x * blockDim.x) {
         const bool isfill = k < nfill;
         const int i = isfill ? d.fill[k] : d.empty[k - nfill];
-        if (!isfill && !(__ldcg(d.flags + i) & B_TOGAS)) continue;
+        if (!isfill && !(d.flags[i] & B_TOGAS)) continue;
         const float m = d.mass[i], r = d.rho[i];
         const float mex = isfill ? m - r : m;
         d.mass[i] = isfill ? r : 0.f;
@@ -268,7 +339,7 @@ __global__ void __launch_bounds__(1024) k_convert(Dev d) {
         cell_coords(d, i, x, y, z);
         int n = 0;
         for (int q = 1; q < Q; ++q) {
-            const uint8_t fj = __ldcg(d.flags + nbr_index(d, x, y, z, cx(q), cy(q), cz(q)));
+            const uint8_t fj = d.flags[nbr_index(d, x, y, z, cx(q), cy(q), cz(q))];
             n += (((fj & T_IF) && !(fj & (B_TOLIQ | B_TOGAS))) || (fj & B_NEW)) ? 1 : 0;
         }
         d.excess[i] = n ? mex / n : 0.f;
@@ -276,75 +347,112 @@ __global__ void __launch_bounds__(1024) k_convert(Dev d) {
     }
 }
 
-// Final types of the step and phi = m / rho of interface cells; interface
-// cells gather the excess mass of converted neighbours in fixed q order and
-// are appended to the interface list of the next step.
-__global__ void __launch_bounds__(256) k_finalize(Dev d) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const bool inb = x < d.nx;
-    const long long i = inb ? cell_index(d, x, y, z) : 0;
-    const uint8_t fl = inb ? d.flags[i] : (uint8_t)0;
+// ---- final update ------------------------------------------------------------
+// A: cells that are interface at t+1 (old interface cells that did not convert,
+//    and the new ones) gather the excess mass of converted neighbours in fixed
+//    q order, set phi = m / rho and form the interface list of t+1.
+__global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
+    const int nold = __ldcg(d.counts + d.cif);
+    const int ngas = __ldcg(d.counts + C_NEWGAS), nliq = __ldcg(d.counts + C_LIQ2IF);
     const bool any = (__ldcg(d.counts + C_FILL) + __ldcg(d.counts + C_EMPTY)) > 0;
-    uint8_t t = fl & T_MASK;
-    if (fl & B_TOLIQ) t = T_LIQ;
-    else if (fl & B_TOGAS) t = T_GAS;
-    else if (fl & B_NEW) t = T_IF;
-    const bool is_if = inb && t == T_IF;
-    if (inb) {
-        if (is_if) {
-            float m = d.mass[i];
-            if (any) {
-                for (int q = 1; q < Q; ++q) {
-                    const long long j = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
-                    if (d.flags[j] & (B_TOLIQ | B_TOGAS)) m += d.excess[j];
+    warp_uniform_loop(nold + ngas + nliq, [&](int k, bool valid) {
+        bool keep = false;
+        int i = 0;
+        if (valid) {
+            i = k < nold ? d.iflist[k] : (k < nold + ngas ? d.newgas[k - nold] : d.liq2if[k - nold - ngas]);
+            const uint8_t fl = d.flags[i];
+            if (!(k < nold && (fl & (B_TOLIQ | B_TOGAS)))) {
+                float m = d.mass[i];
+                if (any) {
+                    int x, y, z;
+                    cell_coords(d, i, x, y, z);
+                    for (int q = 1; q < Q; ++q) {
+                        const int j = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
+                        if (d.flags[j] & (B_TOLIQ | B_TOGAS)) m += d.excess[j];
+                    }
+                    d.mass[i] = m;
                 }
-                d.mass[i] = m;
+                d.phi[i] = m / d.rho[i];
+                keep = true;
             }
-            d.phi[i] = m / d.rho[i];
-        } else if (t != (fl & T_MASK)) {
-            if (t == T_LIQ) {
-                d.phi[i] = 1.0f;
-            } else {
+        }
+        warp_append(d.iflist_next, d.counts + d.cif_next, keep, i);
+    });
+}
+
+// B: final types of the converted cells (transient bits cleared)
+__global__ void __launch_bounds__(LIST_BLOCK) k_fin_b(Dev d) {
+    const int nfill = __ldcg(d.counts + C_FILL), nempty = __ldcg(d.counts + C_EMPTY);
+    const int ngas = __ldcg(d.counts + C_NEWGAS), nliq = __ldcg(d.counts + C_LIQ2IF);
+    const int n = nfill + nempty + ngas + nliq;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (k < nfill) {
+            const int i = d.fill[k];
+            d.flags[i] = T_LIQ | (d.flags[i] & B_NEAR);
+            d.phi[i] = 1.0f;
+        } else if (k < nfill + nempty) {
+            const int i = d.empty[k - nfill];
+            const uint8_t fl = d.flags[i];
+            if (fl & B_TOGAS) {
+                d.flags[i] = T_GAS | (fl & B_NEAR);
                 d.phi[i] = 0.0f;
                 d.mass[i] = 0.0f;
             }
+        } else {
+            const int j = k < nfill + nempty + ngas ? d.newgas[k - nfill - nempty] : d.liq2if[k - nfill - nempty - ngas];
+            d.flags[j] = T_IF | (d.flags[j] & B_NEAR);
         }
-        d.flags_next[i] = t | (fl & B_NEAR);
     }
-    warp_append(d.iflist, d.counts + C_IF, is_if, (int)i);
+}
+
+// active segments -> list (warp-ballot compaction)
+__global__ void __launch_bounds__(256) k_seg_compact(Dev d) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = s < d.nseg && d.seg_active[s];
+    warp_append(d.seg_list, d.counts + C_SEG, act, s);
+}
+
+void launch_seg_compact(const Dev &d, cudaStream_t s) {
+    cudaMemsetAsync(d.counts + C_SEG, 0, sizeof(int), s);
+    k_seg_compact<<<(d.nseg + 255) / 256, 256, 0, s>>>(d);
+}
+
+template <int S, int COLL>
+void launch_sc(const Dev &d, cudaStream_t s) {
+    static const int gb = resident_grid((const void *)k_sc_bulk<S, COLL>, 256);
+    static const int gi = resident_grid((const void *)k_sc_iface<S, COLL>, LIST_BLOCK);
+    k_sc_bulk<S, COLL><<<gb, 256, 0, s>>>(d);
+    k_sc_iface<S, COLL><<<gi, LIST_BLOCK, 0, s>>>(d);
 }
 
 void launch_stream_collide(const Dev &d, cudaStream_t s) {
-    dim3 grid((d.nx + SC_THREADS - 1) / SC_THREADS, d.ny, d.nz);
     const bool trt = d.collision == FSL_TRT;
     switch (d.storage) {
-    case FSL_F32:
-        if (trt) k_stream_collide<FSL_F32, FSL_TRT><<<grid, SC_THREADS, 0, s>>>(d);
-        else k_stream_collide<FSL_F32, FSL_BGK><<<grid, SC_THREADS, 0, s>>>(d);
-        break;
-    case FSL_F16_OFS:
-        if (trt) k_stream_collide<FSL_F16_OFS, FSL_TRT><<<grid, SC_THREADS, 0, s>>>(d);
-        else k_stream_collide<FSL_F16_OFS, FSL_BGK><<<grid, SC_THREADS, 0, s>>>(d);
-        break;
-    default:
-        if (trt) k_stream_collide<FSL_BF16_OFS, FSL_TRT><<<grid, SC_THREADS, 0, s>>>(d);
-        else k_stream_collide<FSL_BF16_OFS, FSL_BGK><<<grid, SC_THREADS, 0, s>>>(d);
-        break;
+    case FSL_F32: trt ? launch_sc<FSL_F32, FSL_TRT>(d, s) : launch_sc<FSL_F32, FSL_BGK>(d, s); break;
+    case FSL_F16_OFS: trt ? launch_sc<FSL_F16_OFS, FSL_TRT>(d, s) : launch_sc<FSL_F16_OFS, FSL_BGK>(d, s); break;
+    default: trt ? launch_sc<FSL_BF16_OFS, FSL_TRT>(d, s) : launch_sc<FSL_BF16_OFS, FSL_BGK>(d, s); break;
     }
 }
 
+int small_grid() { return resident_grid((const void *)k_conv_b, LIST_BLOCK); }
+
 void launch_convert(const Dev &d, cudaStream_t s) {
+    static const int g = small_grid();
+    k_conv_a<<<g, LIST_BLOCK, 0, s>>>(d);
+    k_conv_b<<<g, LIST_BLOCK, 0, s>>>(d);
     switch (d.storage) {
-    case FSL_F32: k_convert<FSL_F32><<<1, 1024, 0, s>>>(d); break;
-    case FSL_F16_OFS: k_convert<FSL_F16_OFS><<<1, 1024, 0, s>>>(d); break;
-    default: k_convert<FSL_BF16_OFS><<<1, 1024, 0, s>>>(d); break;
+    case FSL_F32: k_conv_c<FSL_F32><<<g, LIST_BLOCK, 0, s>>>(d); break;
+    case FSL_F16_OFS: k_conv_c<FSL_F16_OFS><<<g, LIST_BLOCK, 0, s>>>(d); break;
+    default: k_conv_c<FSL_BF16_OFS><<<g, LIST_BLOCK, 0, s>>>(d); break;
     }
+    k_conv_d<<<g, LIST_BLOCK, 0, s>>>(d);
 }
 
 void launch_finalize(const Dev &d, cudaStream_t s) {
-    dim3 grid((d.nx + 255) / 256, d.ny, d.nz);
-    k_finalize<<<grid, 256, 0, s>>>(d);
+    static const int g = resident_grid((const void *)k_fin_a, LIST_BLOCK);
+    k_fin_a<<<g, LIST_BLOCK, 0, s>>>(d);
+    k_fin_b<<<small_grid(), LIST_BLOCK, 0, s>>>(d);
+    launch_seg_compact(d, s);
 }
 
 }  // namespace fslk

@@ -96,7 +96,7 @@ def check(rc: int, what: str = ""):
         raise FslError(f"{what}: {msg} ({rc})")
 
 
-def make_params(shape, collision=BGK, curv_model=CURV_LSQR, storage=F32, storage_shift=8, plic_iters=30, tau=1.0,
+def make_params(shape, collision=BGK, curv_model=CURV_LSQR, storage=F32, storage_shift=8, plic_iters=4, tau=1.0,
                 magic=3.0 / 16.0, sigma=0.0, p_gas=1.0 / 3.0, theta=math.pi / 2, eps_convert=1e-3,
                 lsqr_fp64_cond=1e3) -> Params:
     """shape = (nz, ny, nx) of the numpy/torch arrays (x fastest)."""
@@ -214,7 +214,7 @@ class Sim:
         return self.f[self.parity]
 
     def flags_current(self) -> torch.Tensor:
-        return self.flags[self.parity][: self.N].view(self.shape)
+        return self.flags[0][: self.N].view(self.shape)
 
     def pdfs_float(self) -> torch.Tensor:
         """Current PDFs decoded to float32 (16-bit offsets: f = w_q + v 2^-shift)."""
@@ -234,7 +234,7 @@ class Sim:
             fx = (fx - w) * (2.0 ** self.p.storage_shift)
         self.f[p].copy_(fx.to(dt))
         fl = torch.as_tensor(np.ascontiguousarray(flags, dtype=np.uint8)).reshape(-1)
-        self.flags[p][: self.N].copy_(fl)
+        self.flags[0][: self.N].copy_(fl)
         self.mass.copy_(torch.as_tensor(np.ascontiguousarray(mass, dtype=np.float32)))
         self.phi.copy_(torch.as_tensor(np.ascontiguousarray(phi, dtype=np.float32)))
         torch.cuda.synchronize(self.device)

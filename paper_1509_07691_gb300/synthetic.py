@@ -14,6 +14,8 @@ Workloads (geometry shapes follow the paper's test cases, Sec. III):
                 sigma = 5e-4, theta in {30, 60, 90, 120} degrees
   oscillating256  256^3 periodic, P2-perturbed sphere (amplitude 0.1 R,
                 volume of R = 40), sigma = 1e-3, tau = 0.6
+  oscillating128  the same at half the size (128^3, R = 20): the small case
+                for detailed kernel profiles
   sessile64     64^3, wall layers at z = 0 and z = 63, hemisphere R = 16,
                 TRT tau = 0.8
   coalescence384  384^3, spheres R = 48 and R = 32 with a 4-cell gap,
@@ -78,6 +80,9 @@ WORKLOADS = {
                        geometry=dict(kind="cap", R=30.0, base=(64.0, 64.0, 0.5), zw=0.5), walls=(0, 63)),
     "oscillating256": dict(shape=(256, 256, 256), collision="bgk", tau=0.6, sigma=1e-3, theta_deg=90.0,
                            steps=1000, geometry=dict(kind="mode2", R=40.0, eps2=0.1, base=(128.0, 128.0, 128.0)),
+                           walls=()),
+    "oscillating128": dict(shape=(128, 128, 128), collision="bgk", tau=0.6, sigma=1e-3, theta_deg=90.0,
+                           steps=1000, geometry=dict(kind="mode2", R=20.0, eps2=0.1, base=(64.0, 64.0, 64.0)),
                            walls=()),
     "sessile64": dict(shape=(64, 64, 64), collision="trt", tau=0.8, sigma=2e-4, theta_deg=90.0, steps=50,
                       geometry=dict(kind="cap", R=16.0, base=(32.0, 32.0, 0.5), zw=0.5), walls=(0, 63)),
