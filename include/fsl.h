@@ -86,8 +86,9 @@ typedef struct fsl_params {
     double p_gas;           /* gas pressure p_g (1/3 gives rho_b = 1 at sigma = 0) */
     double theta;           /* equilibrium contact angle theta_eq, radians */
     double eps_convert;     /* conversion threshold eps, e.g. 1e-3 */
-    double lsqr_fp64_cond;  /* re-solve an LSQR cell in FP64 when max|R_jj|/min|R_jj|
-                               of its FP32 QR exceeds this (1e3: normal equations 1e6) */
+    double lsqr_fp64_cond;  /* condition estimate of the LSQR normal equations A^T A,
+                               (max R_jj / min R_jj)^2 of its FP32 factor, above which
+                               the cell is re-solved in FP64 (e.g. 1e6) */
 } fsl_params;
 
 /* Caller-owned device buffers (all 256-byte aligned). */

@@ -14,7 +14,9 @@ struct fsl_ctx {
     fsl_params p;
     fsl_fields fields;
     cudaStream_t stream;     // caller's stream
-    cudaStream_t cap_stream; // private stream used only to record graphs
+    cudaStream_t cap_stream; // private streams used only to record graphs
+    cudaStream_t cap_side;   // (the bulk stream-collide runs on a parallel branch)
+    cudaEvent_t fork, join;
     int parity;
     Dev base;                // pointers and parameters common to both parities
     cudaGraphExec_t graph[2];
@@ -162,13 +164,20 @@ void enqueue_curvature(const Dev &d, int model, float *kappa_out, cudaStream_t s
     else launch_zero_kappa(d, kappa_out, s);
 }
 
-// one time step from parity p (see fsl_step)
-int enqueue_step(const fsl_ctx *c, int parity, cudaStream_t s) {
+// One time step from parity p (see fsl_step), recorded as a graph with two
+// branches: the liquid stream-collide does not need the curvature, so it runs
+// beside normals -> LSQR -> interface stream-collide; both join before the
+// conversion.  The counters of the step are zeroed by its first kernel.
+int enqueue_step_graph(const fsl_ctx *c, int parity) {
     const Dev d = dev_for(c, parity);
+    cudaStream_t s = c->cap_stream, side = c->cap_side;
+    CK(cudaEventRecord(c->fork, s));
+    CK(cudaStreamWaitEvent(side, c->fork, 0));
+    launch_sc_bulk(d, side);
+    CK(cudaEventRecord(c->join, side));
     enqueue_curvature(d, c->p.curv_model, d.kappa, s);
-    CK(cudaMemsetAsync(d.counts + C_FILL, 0, 4 * sizeof(int), s));  // fill, empty, newgas, liq2if
-    CK(cudaMemsetAsync(d.counts + d.cif_next, 0, sizeof(int), s));
-    launch_stream_collide(d, s);
+    launch_sc_iface(d, s);
+    CK(cudaStreamWaitEvent(s, c->join, 0));
     launch_convert(d, s);
     launch_finalize(d, s);
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
@@ -177,7 +186,7 @@ int enqueue_step(const fsl_ctx *c, int parity, cudaStream_t s) {
 int record_graph(fsl_ctx *c, int parity) {
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = enqueue_step(c, parity, c->cap_stream);
+    const int rc = enqueue_step_graph(c, parity);
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     if (rc != FSL_OK || e != cudaSuccess) return FSL_ECUDA;
     e = cudaGraphInstantiate(&c->graph[parity], g, 0);
@@ -222,6 +231,9 @@ int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *ph
     int rc = FSL_ECUDA;
     do {
         if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) break;
+        if (cudaStreamCreateWithFlags(&c->cap_side, cudaStreamNonBlocking) != cudaSuccess) break;
+        if (cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess) break;
+        if (cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) break;
         if (cudaMallocHost((void **)&c->host_mass, 2 * sizeof(double)) != cudaSuccess) break;
         if (cudaMallocHost((void **)&c->host_stats, 16 * sizeof(long long)) != cudaSuccess) break;
         const size_t N = (size_t)c->base.N;
@@ -297,8 +309,6 @@ int fsl_step_profile(fsl_ctx *c, float ms_out[5]) {
         if (c->p.curv_model == FSL_CURV_LSQR) launch_lsqr(d, d.kappa, s);
         else if (c->p.curv_model == FSL_CURV_FD) launch_fd(d, d.kappa, s);
         else launch_zero_kappa(d, d.kappa, s);
-        if (cudaMemsetAsync(d.counts + C_FILL, 0, 4 * sizeof(int), s) != cudaSuccess) break;
-        if (cudaMemsetAsync(d.counts + d.cif_next, 0, sizeof(int), s) != cudaSuccess) break;
         if (cudaEventRecord(ev[2], s) != cudaSuccess) break;
         launch_stream_collide(d, s);
         if (cudaEventRecord(ev[3], s) != cudaSuccess) break;
@@ -318,7 +328,6 @@ int fsl_step_profile(fsl_ctx *c, float ms_out[5]) {
 int fsl_curvature(fsl_ctx *c, int model, float *kappa_out) {
     if (!c || !kappa_out || model < FSL_CURV_LSQR || model > FSL_CURV_NONE) return FSL_EINVAL;
     const Dev d = dev_for(c, c->parity);
-    CK(cudaMemsetAsync(d.counts + C_FP64, 0, sizeof(int), c->stream));
     enqueue_curvature(d, model, kappa_out, c->stream);
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
 }
@@ -377,6 +386,9 @@ void fsl_destroy(fsl_ctx *c) {
     for (int k = 0; k < 2; ++k)
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->cap_side) cudaStreamDestroy(c->cap_side);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
     if (c->host_mass) cudaFreeHost(c->host_mass);
     if (c->host_stats) cudaFreeHost(c->host_stats);
     delete c;

@@ -163,6 +163,42 @@ __device__ __forceinline__ void warp_append(int *list, int *count, bool pred, in
     if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = value;
 }
 
+// Device-side list lengths read once per block (by the first threads, from
+// L2) and broadcast through shared memory: every warp reading a counter
+// itself would queue thousands of requests on the one L2 slice that holds
+// it.  Call once per kernel, from all threads, before any early exit.
+template <int K>
+__device__ __forceinline__ void block_counts(const int *counts, const int (&idx)[K], int (&out)[K]) {
+    __shared__ int sh[K];
+    if (threadIdx.x < K) sh[threadIdx.x] = __ldcg(counts + idx[threadIdx.x]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = sh[k];
+}
+
+// Block-aggregated append: one global atomic per block.  Every thread of the
+// block must call it (block-uniform control flow; blockDim.x <= 1024).
+__device__ __forceinline__ void block_append(int *list, int *count, bool pred, int value) {
+    __shared__ int warp_cnt[32];
+    __shared__ int base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (lane == 0) warp_cnt[warp] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int total = 0;
+        for (int w = 0; w < nwarp; ++w) {
+            const int c = warp_cnt[w];
+            warp_cnt[w] = total;
+            total += c;
+        }
+        base = total ? atomicAdd(count, total) : 0;
+    }
+    __syncthreads();
+    if (pred) list[base + warp_cnt[warp] + __popc(m & ((1u << lane) - 1u))] = value;
+    __syncthreads();
+}
+
 // Loop of a list kernel with a warp-uniform trip count, so that warp_append can
 // be used inside: calls body(k, valid) for k = base + lane.
 template <typename Body>
@@ -187,6 +223,8 @@ void launch_seg_compact(const Dev &d, cudaStream_t s);
 void launch_stats(const Dev &d, cudaStream_t s);
 void launch_mass(const Dev &d, double *out, cudaStream_t s);
 void launch_stream_collide(const Dev &d, cudaStream_t s);
+void launch_sc_bulk(const Dev &d, cudaStream_t s);
+void launch_sc_iface(const Dev &d, cudaStream_t s);
 void launch_convert(const Dev &d, cudaStream_t s);
 void launch_finalize(const Dev &d, cudaStream_t s);
 void launch_normals(const Dev &d, cudaStream_t s);
@@ -197,5 +235,7 @@ void launch_zero_kappa(const Dev &d, float *kappa_out, cudaStream_t s);
 int max_partials();
 // blocks of `block` threads of `kernel` that are resident on the whole GPU at once
 int resident_grid(const void *kernel, int block, size_t smem = 0);
+// grid of the list kernels: `per_sm` blocks per SM, capped at the resident grid
+int list_blocks(const void *kernel, int block, int per_sm);
 
 }  // namespace fslk

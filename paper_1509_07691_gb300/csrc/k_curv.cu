@@ -154,8 +154,17 @@ __device__ float plic_offset(float nx, float ny, float nz, float phi, int iters)
     return M * (0.5f - plic_alpha(m1, m2, m3, phi, iters));
 }
 
+// The first kernel of a step also zeroes that step's counters (conversion
+// lists, general-path LSQR list, FP64 re-solves, next interface list); every
+// later kernel of the step is ordered after it on the stream.
 __global__ void __launch_bounds__(LIST_THREADS) k_normals(Dev d) {
-    const int n = __ldcg(d.counts + d.cif);
+    int cnt[1];
+    block_counts<1>(d.counts, {d.cif}, cnt);
+    const int n = cnt[0];
+    if (blockIdx.x == 0 && threadIdx.x < 8) {
+        const int zero[8] = {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF, C_SLOW, C_FP64, d.cif_next, d.cif_next};
+        d.counts[zero[threadIdx.x]] = 0;
+    }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = d.iflist[k];
         int x, y, z;
@@ -445,15 +454,16 @@ __device__ float lsqr_cell(const Dev &d, int i, int x, int y, int z, float &cond
     return (float)((A * (T(1) + I * I) + B * (T(1) + H * H) - C * H * I) / (g * sqrt(g)));
 }
 
-// Fast path: FP32 fit of the full model for an interface cell with no
-// contact-line cell in its neighbourhood.  Returns false (cell left to the
-// general path) when a contact-line cell is present, when there are fewer
-// than five rows, or when R is rank deficient or ill conditioned.
+// Fast path: FP32 normal equations of the full model for an interface cell
+// with no contact-line cell in its neighbourhood.  The 5x5 Gram matrix
+// A^T A and A^T f are accumulated row by row (independent FMAs), then solved
+// by Cholesky in registers.  Returns false (cell left to the general path)
+// when a contact-line cell is present, when there are fewer than five rows,
+// or when the Cholesky pivots estimate cond(A^T A) above d.fp64_cond.
 __device__ bool lsqr_fast(const Dev &d, int i, int x, int y, int z, float &kap) {
     const float4 c4 = d.normal[i];
     kap = 0.f;
     if (c4.x == 0.f && c4.y == 0.f && c4.z == 0.f) return true;
-    if (d.flags[i] & B_NEAR) return false;
     const float n[3] = {c4.x, c4.y, c4.z};
     int k = 0;
     if (fabsf(n[1]) < fabsf(n[0])) k = 1;
@@ -468,49 +478,103 @@ __device__ bool lsqr_fast(const Dev &d, int i, int x, int y, int z, float &kap) 
     tu[2] *= tl;
     const float tv[3] = {n[1] * tu[2] - n[2] * tu[1], n[2] * tu[0] - n[0] * tu[2], n[0] * tu[1] - n[1] * tu[0]};
     const float p[3] = {c4.w * n[0], c4.w * n[1], c4.w * n[2]};
-    Givens<float, 5> full;
-    full.init();
+    float G[15], r[5];
+#pragma unroll
+    for (int t = 0; t < 15; ++t) G[t] = 0.f;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) r[t] = 0.f;
     int m = 0;
+    bool contact = (d.flags[i] & B_NEAR) != 0;
     const int xs[3] = {x == 0 ? d.nx - 1 : x - 1, x, x == d.nx - 1 ? 0 : x + 1};
     const int ys[3] = {y == 0 ? d.ny - 1 : y - 1, y, y == d.ny - 1 ? 0 : y + 1};
-    const int zs[3] = {z == 0 ? d.nz - 1 : z - 1, z, z == d.nz - 1 ? 0 : z + 1};
 #pragma unroll 1
     for (int pz = 0; pz < 3; ++pz) {
+        const int zz = z + pz - 1 < 0 ? d.nz - 1 : (z + pz - 1 >= d.nz ? 0 : z + pz - 1);
         int jj[9];
         uint8_t fjs[9];
         float4 q4s[9];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) jj[t] = cell_index(d, xs[t % 3], ys[t / 3], zs[pz]);
+        for (int t = 0; t < 9; ++t) jj[t] = cell_index(d, xs[t % 3], ys[t / 3], zz);
 #pragma unroll
         for (int t = 0; t < 9; ++t) fjs[t] = d.flags[jj[t]];
 #pragma unroll
         for (int t = 0; t < 9; ++t) q4s[t] = d.normal[jj[t]];
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
-            if (pz == 1 && t == 4) continue;
-            if (!(fjs[t] & T_IF)) continue;
-            if (fjs[t] & B_NEAR) return false;
             const float4 q4 = q4s[t];
-            if (q4.x == 0.f && q4.y == 0.f && q4.z == 0.f) continue;
+            const bool use = (fjs[t] & T_IF) && !(pz == 1 && t == 4) && !(q4.x == 0.f && q4.y == 0.f && q4.z == 0.f);
+            contact |= (fjs[t] & T_IF) && (fjs[t] & B_NEAR);
+            const float w = use ? 1.f : 0.f;
             const float dv[3] = {(float)(t % 3 - 1) + q4.w * q4.x - p[0], (float)(t / 3 - 1) + q4.w * q4.y - p[1],
                                  (float)(pz - 1) + q4.w * q4.z - p[2]};
-            const float u = dot3(dv, tu), v = dot3(dv, tv), f = dot3(dv, n);
-            float rf[5] = {u * u, v * v, u * v, u, v};
-            full.add(rf, f, 5);
-            ++m;
+            const float u = dot3(dv, tu), v = dot3(dv, tv), f = w * dot3(dv, n);
+            const float a[5] = {w * u * u, w * v * v, w * u * v, w * u, w * v};
+            int c = 0;
+#pragma unroll
+            for (int a0 = 0; a0 < 5; ++a0) {
+#pragma unroll
+                for (int a1 = a0; a1 < 5; ++a1) G[c++] += a[a0] * a[a1];
+                r[a0] += a[a0] * f;
+            }
+            m += use ? 1 : 0;
         }
     }
-    if (m < 5) return false;
-    float sol[5], cond;
-    if (!full.solve(sol, 5, cond) || cond > d.fp64_cond) return false;
+    // Cholesky G = R^T R (R upper, packed like G)
+    float R[15];
+    float dmax = 0.f, dmin = 3.0e38f;
+    bool pd = true;
+    {
+        int c = 0;
+#pragma unroll
+        for (int a0 = 0; a0 < 5; ++a0) {
+#pragma unroll
+            for (int a1 = a0; a1 < 5; ++a1, ++c) {
+                float sum = G[c];
+#pragma unroll
+                for (int kk = 0; kk < a0; ++kk) {
+                    const int i0 = kk * 5 - kk * (kk - 1) / 2 + (a0 - kk), i1 = kk * 5 - kk * (kk - 1) / 2 + (a1 - kk);
+                    sum -= R[i0] * R[i1];
+                }
+                if (a1 == a0) {
+                    pd = pd && sum > 0.f;
+                    const float dd = sqrtf(fmaxf(sum, 1e-30f));
+                    R[c] = dd;
+                    dmax = fmaxf(dmax, dd);
+                    dmin = fminf(dmin, dd);
+                } else {
+                    R[c] = sum / R[a0 * 5 - a0 * (a0 - 1) / 2];
+                }
+            }
+        }
+    }
+    const float cond = (dmax / dmin) * (dmax / dmin);
+    const bool ok = !contact && m >= 5 && pd && !(cond > d.fp64_cond);
+    // R^T y = r, R x = y
+    float yv[5], sol[5];
+#pragma unroll
+    for (int a0 = 0; a0 < 5; ++a0) {
+        float sum = r[a0];
+#pragma unroll
+        for (int kk = 0; kk < a0; ++kk) sum -= R[kk * 5 - kk * (kk - 1) / 2 + (a0 - kk)] * yv[kk];
+        yv[a0] = sum / R[a0 * 5 - a0 * (a0 - 1) / 2];
+    }
+#pragma unroll
+    for (int a0 = 4; a0 >= 0; --a0) {
+        float sum = yv[a0];
+#pragma unroll
+        for (int kk = a0 + 1; kk < 5; ++kk) sum -= R[a0 * 5 - a0 * (a0 - 1) / 2 + (kk - a0)] * sol[kk];
+        sol[a0] = sum / R[a0 * 5 - a0 * (a0 - 1) / 2];
+    }
     const float A = sol[0], B = sol[1], C = sol[2], H = sol[3], I = sol[4];
     const float g = 1.0f + H * H + I * I;
     kap = (A * (1.0f + I * I) + B * (1.0f + H * H) - C * H * I) / (g * sqrtf(g));
-    return true;
+    return ok;
 }
 
 __global__ void __launch_bounds__(LIST_THREADS) k_lsqr_fast(Dev d, float *kappa_out) {
-    const int n = __ldcg(d.counts + d.cif);
+    int cnt[1];
+    block_counts<1>(d.counts, {d.cif}, cnt);
+    const int n = cnt[0];
     warp_uniform_loop(n, [&](int k, bool valid) {
         bool defer = false;
         int i = 0;
@@ -529,14 +593,16 @@ __global__ void __launch_bounds__(LIST_THREADS) k_lsqr_fast(Dev d, float *kappa_
 // General path: contact rows and centre constraint, isotropic fallback, FP64
 // re-solve when the FP32 R is ill conditioned
 __global__ void __launch_bounds__(LIST_THREADS) k_lsqr_slow(Dev d, float *kappa_out) {
-    const int n = __ldcg(d.counts + C_SLOW);
+    int cnt[1];
+    block_counts<1>(d.counts, {C_SLOW}, cnt);
+    const int n = cnt[0];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = d.slow[k];
         int x, y, z;
         cell_coords(d, i, x, y, z);
         float cond;
         float kap = lsqr_cell<float>(d, i, x, y, z, cond);
-        if (cond > d.fp64_cond) {
+        if (cond * cond > d.fp64_cond) {
             kap = lsqr_cell<double>(d, i, x, y, z, cond);
             atomicAdd(d.counts + C_FP64, 1);
         }
@@ -625,7 +691,9 @@ __device__ void fd_normal(const Dev &d, int x, int y, int z, float n[3]) {
 }
 
 __global__ void __launch_bounds__(LIST_THREADS) k_fd(Dev d, float *kappa_out) {
-    const int n = __ldcg(d.counts + d.cif);
+    int cnt[1];
+    block_counts<1>(d.counts, {d.cif}, cnt);
+    const int n = cnt[0];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = d.iflist[k];
         int x, y, z;
@@ -645,27 +713,28 @@ __global__ void __launch_bounds__(LIST_THREADS) k_fd(Dev d, float *kappa_out) {
 }
 
 __global__ void k_zero_kappa(Dev d, float *kappa_out) {
-    const int n = __ldcg(d.counts + d.cif);
+    int cnt[1];
+    block_counts<1>(d.counts, {d.cif}, cnt);
+    const int n = cnt[0];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) kappa_out[d.iflist[k]] = 0.f;
 }
 
 void launch_normals(const Dev &d, cudaStream_t s) {
-    static const int g = resident_grid((const void *)k_normals, LIST_THREADS);
+    static const int g = list_blocks((const void *)k_normals, LIST_THREADS, 4);
     k_normals<<<g, LIST_THREADS, 0, s>>>(d);
 }
 void launch_lsqr(const Dev &d, float *kappa_out, cudaStream_t s) {
-    static const int gf = resident_grid((const void *)k_lsqr_fast, LIST_THREADS);
-    static const int gs = resident_grid((const void *)k_lsqr_slow, LIST_THREADS);
-    cudaMemsetAsync(d.counts + C_SLOW, 0, sizeof(int), s);
+    static const int gf = list_blocks((const void *)k_lsqr_fast, LIST_THREADS, 4);
+    static const int gs = list_blocks((const void *)k_lsqr_slow, LIST_THREADS, 1);
     k_lsqr_fast<<<gf, LIST_THREADS, 0, s>>>(d, kappa_out);
     k_lsqr_slow<<<gs, LIST_THREADS, 0, s>>>(d, kappa_out);
 }
 void launch_fd(const Dev &d, float *kappa_out, cudaStream_t s) {
-    static const int g = resident_grid((const void *)k_fd, LIST_THREADS);
+    static const int g = list_blocks((const void *)k_fd, LIST_THREADS, 4);
     k_fd<<<g, LIST_THREADS, 0, s>>>(d, kappa_out);
 }
 void launch_zero_kappa(const Dev &d, float *kappa_out, cudaStream_t s) {
-    static const int g = resident_grid((const void *)k_zero_kappa, LIST_THREADS);
+    static const int g = list_blocks((const void *)k_zero_kappa, LIST_THREADS, 4);
     k_zero_kappa<<<g, LIST_THREADS, 0, s>>>(d, kappa_out);
 }
 

@@ -12,6 +12,14 @@ int resident_grid(const void *kernel, int block, size_t smem) {
     return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
 }
 
+int list_blocks(const void *kernel, int block, int per_sm) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int want = (sms > 0 ? sms : 1) * per_sm, cap = resident_grid(kernel, block);
+    return want < cap ? want : cap;
+}
+
 // ---- fill levels -------------------------------------------------------------
 // Inside tests in FP64 with explicitly rounded operations (no contraction),
 // evaluated in the same order as the sampling formula states, so that every

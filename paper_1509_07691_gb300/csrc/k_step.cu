@@ -70,7 +70,9 @@ __device__ __forceinline__ void sources(const Dev &d, int x, int y, int z, int s
 template <int S, int COLL>
 __global__ void __launch_bounds__(256) k_sc_bulk(Dev d) {
     using St = Store<S>;
-    const int nseg = __ldcg(d.counts + C_SEG);
+    int cnt[1];
+    block_counts<1>(d.counts, {C_SEG}, cnt);
+    const int nseg = cnt[0];
     const long long N = d.N;
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -107,7 +109,8 @@ __global__ void __launch_bounds__(256) k_sc_bulk(Dev d) {
     }
 }
 
-// Interface cells (list): each link by the type of its source cell x - c_q:
+// Interface cells (list), one thread per cell.  Each link is resolved by
+// the type of its source cell x - c_q:
 //   fluid     f_q(x) = f'_q(x - c_q)                        (Eq. lbe1)
 //   gas       f_q(x) = feq_q + feq_qbar - f'_qbar(x)         (Eq. reconstruct)
 //             with rho_b = 3 p_g + 6 sigma kappa(x), u_b = u(x, t)
@@ -118,95 +121,95 @@ __global__ void __launch_bounds__(256) k_sc_bulk(Dev d) {
 template <int S, int COLL>
 __global__ void __launch_bounds__(LIST_BLOCK) k_sc_iface(Dev d) {
     using St = Store<S>;
-    const int n = __ldcg(d.counts + d.cif);
+    int cnt[1];
+    block_counts<1>(d.counts, {d.cif}, cnt);
+    const int n = cnt[0];
     const long long N = d.N;
-    warp_uniform_loop(n, [&](int k, bool valid) {
-        bool fill = false, empty = false;
-        int i = 0;
-        if (valid) {
-            i = d.iflist[k];
-            int x, y, z;
-            cell_coords(d, i, x, y, z);
-            int src[Q];
-            sources(d, x, y, z, src);
-            const uint8_t fl = d.flags[i];
-            float fo[Q], f[Q];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int i = d.iflist[k];
+        int x, y, z;
+        cell_coords(d, i, x, y, z);
+        int src[Q];
+        sources(d, x, y, z, src);
+        const uint8_t fl = d.flags[i];
+        float fo[Q], f[Q];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) fo[q] = St::ld(d.fsrc, (long long)q * N + i, q, d);
-            uint8_t tq[Q];
-            bool has_gas = false, has_obs = false;
-            float wx = 0.f, wy = 0.f, wz = 0.f;  // sum of vectors x -> obstacle neighbour
+        for (int q = 0; q < Q; ++q) fo[q] = St::ld(d.fsrc, (long long)q * N + i, q, d);
+        uint8_t tq[Q];
+        bool has_gas = false, has_obs = false;
+        float wx = 0.f, wy = 0.f, wz = 0.f;  // sum of vectors x -> obstacle neighbour
 #pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                tq[q] = d.flags[src[q]] & T_MASK;
-                has_gas |= (tq[q] & T_GAS) != 0;
-                if (tq[q] & T_OBS) {
-                    has_obs = true;
-                    wx -= cx(q);
-                    wy -= cy(q);
-                    wz -= cz(q);
-                }
+        for (int q = 1; q < Q; ++q) {
+            tq[q] = d.flags[src[q]] & T_MASK;
+            has_gas |= (tq[q] & T_GAS) != 0;
+            if (tq[q] & T_OBS) {
+                has_obs = true;
+                wx -= cx(q);
+                wy -= cy(q);
+                wz -= cz(q);
             }
-            // u_b: velocity of x at time t from its own post-collision PDFs
-            float r0 = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                r0 += fo[q];
-                jx += cx(q) * fo[q];
-                jy += cy(q) * fo[q];
-                jz += cz(q) * fo[q];
-            }
-            const float ux = jx / r0, uy = jy / r0, uz = jz / r0;
-            const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
-            const float rho_b = d.rho_gas + d.six_sigma * d.kappa[i];
-            const bool corner = has_gas && has_obs;
-            float ntx = 0.f, nty = 0.f, ntz = 0.f;
-            if (corner) {
-                const float4 n4 = d.normal[i];
-                const float wl = rsqrtf(wx * wx + wy * wy + wz * wz);
-                wx *= wl;
-                wy *= wl;
-                wz *= wl;
-                const float wn = n4.x * wx + n4.y * wy + n4.z * wz;
-                ntx = n4.x - wn * wx;
-                nty = n4.y - wn * wy;
-                ntz = n4.z - wn * wz;
-            }
-            const float phix = d.phi[i];
-            float dm = 0.f;
-            f[0] = fo[0];
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                const int qb = opp(q);
-                const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-                // feq_q + feq_qbar at (rho_b, u_b): the odd terms cancel
-                const float recon = 2.0f * wq(q) * rho_b * (1.0f + 4.5f * cu * cu - uu) - fo[qb];
-                if (tq[q] & (T_LIQ | T_IF)) {
-                    const float fin = St::ld(d.fsrc, (long long)q * N + src[q], q, d);
-                    f[q] = fin;
-                    const float kq = (tq[q] & T_LIQ) ? 1.0f : 0.5f * (phix + d.phi[src[q]]);
-                    dm += kq * (fin - fo[qb]);
-                } else if (tq[q] & T_OBS) {
-                    const float outdir = -(cx(q) * ntx + cy(q) * nty + cz(q) * ntz);  // c_qbar . n_t
-                    f[q] = (corner && outdir < 0.f) ? recon : fo[qb];
-                } else {
-                    f[q] = recon;
-                }
-            }
-            float rho;
-            collide<COLL>(f, d, rho);
-#pragma unroll
-            for (int q = 0; q < Q; ++q) St::st(d.fdst, (long long)q * N + i, q, f[q], d);
-            const float m = d.mass[i] + dm;
-            d.mass[i] = m;
-            d.rho[i] = rho;
-            fill = m > (1.0f + d.eps) * rho;
-            empty = !fill && (m < -d.eps * rho);
-            if (fill || empty) d.flags[i] = fl | (fill ? B_TOLIQ : B_TOGAS);
         }
-        warp_append(d.fill, d.counts + C_FILL, fill, i);
-        warp_append(d.empty, d.counts + C_EMPTY, empty, i);
-    });
+        // u_b: velocity of x at time t from its own post-collision PDFs
+        float r0 = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            r0 += fo[q];
+            jx += cx(q) * fo[q];
+            jy += cy(q) * fo[q];
+            jz += cz(q) * fo[q];
+        }
+        const float ux = jx / r0, uy = jy / r0, uz = jz / r0;
+        const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+        const float rho_b = d.rho_gas + d.six_sigma * d.kappa[i];
+        const bool corner = has_gas && has_obs;
+        float ntx = 0.f, nty = 0.f, ntz = 0.f;
+        if (corner) {
+            const float4 n4 = d.normal[i];
+            const float wl = rsqrtf(wx * wx + wy * wy + wz * wz);
+            wx *= wl;
+            wy *= wl;
+            wz *= wl;
+            const float wn = n4.x * wx + n4.y * wy + n4.z * wz;
+            ntx = n4.x - wn * wx;
+            nty = n4.y - wn * wy;
+            ntz = n4.z - wn * wz;
+        }
+        const float phix = d.phi[i];
+        float dm = 0.f;
+        f[0] = fo[0];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            const int qb = opp(q);
+            const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+            // feq_q + feq_qbar at (rho_b, u_b): the odd terms cancel
+            const float recon = 2.0f * wq(q) * rho_b * (1.0f + 4.5f * cu * cu - uu) - fo[qb];
+            if (tq[q] & (T_LIQ | T_IF)) {
+                const float fin = St::ld(d.fsrc, (long long)q * N + src[q], q, d);
+                f[q] = fin;
+                const float kq = (tq[q] & T_LIQ) ? 1.0f : 0.5f * (phix + d.phi[src[q]]);
+                dm += kq * (fin - fo[qb]);
+            } else if (tq[q] & T_OBS) {
+                const float outdir = -(cx(q) * ntx + cy(q) * nty + cz(q) * ntz);  // c_qbar . n_t
+                f[q] = (corner && outdir < 0.f) ? recon : fo[qb];
+            } else {
+                f[q] = recon;
+            }
+        }
+        float rho;
+        collide<COLL>(f, d, rho);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) St::st(d.fdst, (long long)q * N + i, q, f[q], d);
+        const float m = d.mass[i] + dm;
+        d.mass[i] = m;
+        d.rho[i] = rho;
+        if (m > (1.0f + d.eps) * rho) {
+            d.flags[i] = fl | B_TOLIQ;
+            d.fill[atomicAdd(d.counts + C_FILL, 1)] = i;
+        } else if (m < -d.eps * rho) {
+            d.flags[i] = fl | B_TOGAS;
+            d.empty[atomicAdd(d.counts + C_EMPTY, 1)] = i;
+        }
+    }
 }
 
 // ---- conversion (the paper cites Koerner et al. for it; readings) -------------
@@ -218,9 +221,18 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_sc_iface(Dev d) {
 //  D  the excess mass (m - rho of a filled cell, m of an emptied one) is
 //     divided equally among the neighbours that are interface after B; the
 //     receivers gather it in k_fin_a.  No receiver: added to `lost`.
-__global__ void __launch_bounds__(LIST_BLOCK) k_conv_a(Dev d) {
-    const int nempty = __ldcg(d.counts + C_EMPTY);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nempty; k += gridDim.x * blockDim.x) {
+// One block of 1024 threads with block barriers between the phases: a step
+// converts few cells, and one block keeps every phase visible to the next.
+constexpr int CONV_BLOCK = 1024;
+
+template <int S>
+__global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
+    using St = Store<S>;
+    const int nfill = __ldcg(d.counts + C_FILL), nempty = __ldcg(d.counts + C_EMPTY);
+    if (nfill + nempty == 0) return;
+    const long long N = d.N;
+    // A
+    for (int k = threadIdx.x; k < nempty; k += blockDim.x) {
         const int i = d.empty[k];
         int x, y, z;
         cell_coords(d, i, x, y, z);
@@ -230,14 +242,12 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_conv_a(Dev d) {
                 break;
             }
     }
-}
-
-__global__ void __launch_bounds__(LIST_BLOCK) k_conv_b(Dev d) {
-    const int nfill = __ldcg(d.counts + C_FILL), nempty = __ldcg(d.counts + C_EMPTY);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nfill + nempty; k += gridDim.x * blockDim.x) {
+    __syncthreads();
+    // B
+    for (int k = threadIdx.x; k < nfill + nempty; k += blockDim.x) {
         const bool isfill = k < nfill;
         const int i = isfill ? d.fill[k] : d.empty[k - nfill];
-        if (!isfill && !(d.flags[i] & B_TOGAS)) continue;
+        if (!isfill && !(__ldcg(d.flags + i) & B_TOGAS)) continue;
         int x, y, z;
         cell_coords(d, i, x, y, z);
         for (int q = 1; q < Q; ++q) {
@@ -258,18 +268,11 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_conv_b(Dev d) {
             }
         }
     }
-}
-
-// one warp per new cell; lane q (1..18) reads neighbour x + c_q
-template <int S>
-__global__ void __launch_bounds__(LIST_BLOCK) k_conv_c(Dev d) {
-    using St = Store<S>;
+    __syncthreads();
+    // C: one warp per new cell; lane q (1..18) reads neighbour x + c_q
     const int ngas = __ldcg(d.counts + C_NEWGAS), nliq = __ldcg(d.counts + C_LIQ2IF);
-    const int lane = threadIdx.x & 31;
-    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-    const long long N = d.N;
-    for (int k = gwarp; k < ngas + nliq; k += nwarps) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int k = warp; k < ngas + nliq; k += nwarps) {
         if (k < ngas) {
             const int j = d.newgas[k];
             int x, y, z;
@@ -278,11 +281,11 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_conv_c(Dev d) {
             if (lane >= 1 && lane < Q) {
                 const int q = lane;
                 const int l = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
-                if (d.flags[l] & (T_LIQ | T_IF)) {
+                if (__ldcg(d.flags + l) & (T_LIQ | T_IF)) {
                     float jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
                     for (int p = 0; p < Q; ++p) {
-                        const float v = St::ld(d.fdst, (long long)p * N + l, p, d);
+                        const float v = St::ldcg(d.fdst, (long long)p * N + l, p, d);
                         r += v;
                         jx += cx(p) * v;
                         jy += cy(p) * v;
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_conv_c(Dev d) {
             }
         } else {
             const int j = d.liq2if[k - ngas];
-            float r = lane < Q ? St::ld(d.fdst, (long long)lane * N + j, lane, d) : 0.f;
+            float r = lane < Q ? St::ldcg(d.fdst, (long long)lane * N + j, lane, d) : 0.f;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
             if (lane == 0) {
@@ -324,22 +327,20 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_conv_c(Dev d) {
             }
         }
     }
-}
-
-__global__ void __launch_bounds__(LIST_BLOCK) k_conv_d(Dev d) {
-    const int nfill = __ldcg(d.counts + C_FILL), nempty = __ldcg(d.counts + C_EMPTY);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nfill + nempty; k += gridDim.x * blockDim.x) {
+    __syncthreads();
+    // D
+    for (int k = threadIdx.x; k < nfill + nempty; k += blockDim.x) {
         const bool isfill = k < nfill;
         const int i = isfill ? d.fill[k] : d.empty[k - nfill];
-        if (!isfill && !(d.flags[i] & B_TOGAS)) continue;
-        const float m = d.mass[i], r = d.rho[i];
+        if (!isfill && !(__ldcg(d.flags + i) & B_TOGAS)) continue;
+        const float m = __ldcg(d.mass + i), r = __ldcg(d.rho + i);
         const float mex = isfill ? m - r : m;
         d.mass[i] = isfill ? r : 0.f;
         int x, y, z;
         cell_coords(d, i, x, y, z);
         int n = 0;
         for (int q = 1; q < Q; ++q) {
-            const uint8_t fj = d.flags[nbr_index(d, x, y, z, cx(q), cy(q), cz(q))];
+            const uint8_t fj = __ldcg(d.flags + nbr_index(d, x, y, z, cx(q), cy(q), cz(q)));
             n += (((fj & T_IF) && !(fj & (B_TOLIQ | B_TOGAS))) || (fj & B_NEW)) ? 1 : 0;
         }
         d.excess[i] = n ? mex / n : 0.f;
@@ -352,9 +353,11 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_conv_d(Dev d) {
 //    and the new ones) gather the excess mass of converted neighbours in fixed
 //    q order, set phi = m / rho and form the interface list of t+1.
 __global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
-    const int nold = __ldcg(d.counts + d.cif);
-    const int ngas = __ldcg(d.counts + C_NEWGAS), nliq = __ldcg(d.counts + C_LIQ2IF);
-    const bool any = (__ldcg(d.counts + C_FILL) + __ldcg(d.counts + C_EMPTY)) > 0;
+    int cnt[5];
+    block_counts<5>(d.counts, {d.cif, C_NEWGAS, C_LIQ2IF, C_FILL, C_EMPTY}, cnt);
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.counts[C_SEG] = 0;  // filled again by k_fin_b
+    const int nold = cnt[0], ngas = cnt[1], nliq = cnt[2];
+    const bool any = (cnt[3] + cnt[4]) > 0;
     warp_uniform_loop(nold + ngas + nliq, [&](int k, bool valid) {
         bool keep = false;
         int i = 0;
@@ -380,12 +383,15 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
     });
 }
 
-// B: final types of the converted cells (transient bits cleared)
-__global__ void __launch_bounds__(LIST_BLOCK) k_fin_b(Dev d) {
-    const int nfill = __ldcg(d.counts + C_FILL), nempty = __ldcg(d.counts + C_EMPTY);
-    const int ngas = __ldcg(d.counts + C_NEWGAS), nliq = __ldcg(d.counts + C_LIQ2IF);
+// B: final types of the converted cells (transient bits cleared), and the
+// list of active segments for the next step (warp-ballot compaction)
+__global__ void __launch_bounds__(256) k_fin_b(Dev d) {
+    int cnt[4];
+    block_counts<4>(d.counts, {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF}, cnt);
+    const int nfill = cnt[0], nempty = cnt[1], ngas = cnt[2], nliq = cnt[3];
     const int n = nfill + nempty + ngas + nliq;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (int k = tid; k < n; k += nth) {
         if (k < nfill) {
             const int i = d.fill[k];
             d.flags[i] = T_LIQ | (d.flags[i] & B_NEAR);
@@ -403,9 +409,13 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_fin_b(Dev d) {
             d.flags[j] = T_IF | (d.flags[j] & B_NEAR);
         }
     }
+    for (int base = blockIdx.x * blockDim.x; base < d.nseg; base += nth) {
+        const int s = base + threadIdx.x;
+        block_append(d.seg_list, d.counts + C_SEG, s < d.nseg && d.seg_active[s], s);
+    }
 }
 
-// active segments -> list (warp-ballot compaction)
+// active segments -> list (warp-ballot compaction); counter zeroed first
 __global__ void __launch_bounds__(256) k_seg_compact(Dev d) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = s < d.nseg && d.seg_active[s];
@@ -418,41 +428,49 @@ void launch_seg_compact(const Dev &d, cudaStream_t s) {
 }
 
 template <int S, int COLL>
-void launch_sc(const Dev &d, cudaStream_t s) {
+void launch_bulk(const Dev &d, cudaStream_t s) {
     static const int gb = resident_grid((const void *)k_sc_bulk<S, COLL>, 256);
-    static const int gi = resident_grid((const void *)k_sc_iface<S, COLL>, LIST_BLOCK);
     k_sc_bulk<S, COLL><<<gb, 256, 0, s>>>(d);
+}
+
+template <int S, int COLL>
+void launch_iface(const Dev &d, cudaStream_t s) {
+    static const int gi = list_blocks((const void *)k_sc_iface<S, COLL>, LIST_BLOCK, 4);
     k_sc_iface<S, COLL><<<gi, LIST_BLOCK, 0, s>>>(d);
 }
 
+#define FSL_DISPATCH(FN)                                                                          \
+    do {                                                                                          \
+        const bool trt = d.collision == FSL_TRT;                                                  \
+        switch (d.storage) {                                                                      \
+        case FSL_F32: trt ? FN<FSL_F32, FSL_TRT>(d, s) : FN<FSL_F32, FSL_BGK>(d, s); break;        \
+        case FSL_F16_OFS: trt ? FN<FSL_F16_OFS, FSL_TRT>(d, s) : FN<FSL_F16_OFS, FSL_BGK>(d, s); break; \
+        default: trt ? FN<FSL_BF16_OFS, FSL_TRT>(d, s) : FN<FSL_BF16_OFS, FSL_BGK>(d, s); break;   \
+        }                                                                                         \
+    } while (0)
+
+void launch_sc_bulk(const Dev &d, cudaStream_t s) { FSL_DISPATCH(launch_bulk); }
+void launch_sc_iface(const Dev &d, cudaStream_t s) { FSL_DISPATCH(launch_iface); }
+#undef FSL_DISPATCH
+
 void launch_stream_collide(const Dev &d, cudaStream_t s) {
-    const bool trt = d.collision == FSL_TRT;
-    switch (d.storage) {
-    case FSL_F32: trt ? launch_sc<FSL_F32, FSL_TRT>(d, s) : launch_sc<FSL_F32, FSL_BGK>(d, s); break;
-    case FSL_F16_OFS: trt ? launch_sc<FSL_F16_OFS, FSL_TRT>(d, s) : launch_sc<FSL_F16_OFS, FSL_BGK>(d, s); break;
-    default: trt ? launch_sc<FSL_BF16_OFS, FSL_TRT>(d, s) : launch_sc<FSL_BF16_OFS, FSL_BGK>(d, s); break;
-    }
+    launch_sc_bulk(d, s);
+    launch_sc_iface(d, s);
 }
 
-int small_grid() { return resident_grid((const void *)k_conv_b, LIST_BLOCK); }
-
 void launch_convert(const Dev &d, cudaStream_t s) {
-    static const int g = small_grid();
-    k_conv_a<<<g, LIST_BLOCK, 0, s>>>(d);
-    k_conv_b<<<g, LIST_BLOCK, 0, s>>>(d);
     switch (d.storage) {
-    case FSL_F32: k_conv_c<FSL_F32><<<g, LIST_BLOCK, 0, s>>>(d); break;
-    case FSL_F16_OFS: k_conv_c<FSL_F16_OFS><<<g, LIST_BLOCK, 0, s>>>(d); break;
-    default: k_conv_c<FSL_BF16_OFS><<<g, LIST_BLOCK, 0, s>>>(d); break;
+    case FSL_F32: k_convert<FSL_F32><<<1, CONV_BLOCK, 0, s>>>(d); break;
+    case FSL_F16_OFS: k_convert<FSL_F16_OFS><<<1, CONV_BLOCK, 0, s>>>(d); break;
+    default: k_convert<FSL_BF16_OFS><<<1, CONV_BLOCK, 0, s>>>(d); break;
     }
-    k_conv_d<<<g, LIST_BLOCK, 0, s>>>(d);
 }
 
 void launch_finalize(const Dev &d, cudaStream_t s) {
-    static const int g = resident_grid((const void *)k_fin_a, LIST_BLOCK);
-    k_fin_a<<<g, LIST_BLOCK, 0, s>>>(d);
-    k_fin_b<<<small_grid(), LIST_BLOCK, 0, s>>>(d);
-    launch_seg_compact(d, s);
+    static const int ga = list_blocks((const void *)k_fin_a, LIST_BLOCK, 4);
+    static const int gb = list_blocks((const void *)k_fin_b, 256, 4);
+    k_fin_a<<<ga, LIST_BLOCK, 0, s>>>(d);
+    k_fin_b<<<gb, 256, 0, s>>>(d);
 }
 
 }  // namespace fslk

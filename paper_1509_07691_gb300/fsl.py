@@ -98,7 +98,7 @@ def check(rc: int, what: str = ""):
 
 def make_params(shape, collision=BGK, curv_model=CURV_LSQR, storage=F32, storage_shift=8, plic_iters=4, tau=1.0,
                 magic=3.0 / 16.0, sigma=0.0, p_gas=1.0 / 3.0, theta=math.pi / 2, eps_convert=1e-3,
-                lsqr_fp64_cond=1e3) -> Params:
+                lsqr_fp64_cond=1e6) -> Params:
     """shape = (nz, ny, nx) of the numpy/torch arrays (x fastest)."""
     nz, ny, nx = shape
     return Params(nx, ny, nz, collision, curv_model, storage, storage_shift, plic_iters, tau, magic, sigma, p_gas,
