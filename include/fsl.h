@@ -180,6 +180,28 @@ int fsl_stats(struct fsl_ctx *ctx, int64_t counts_out[8]);
  * conversion, finalize.  For profiling.  Synchronising. */
 int fsl_step_profile(struct fsl_ctx *ctx, float ms_out[5]);
 
+/* Total mass of a state (sum of m over interface cells plus sum of rho over
+ * liquid cells) for callers that cannot allocate device memory: a host
+ * application that owns all device memory through its own allocator or a
+ * fixed budget, or monitoring code in a time-critical loop that must not pay
+ * for an allocation.  The paper has no counterpart; it is a service of this
+ * library.  The caller passes the state (f: the current PDF buffer, storage
+ * per params; flags; mass) and one device double for the result.  Nothing is
+ * allocated: the block partial sums go to a fixed FP64 array of
+ * FSL_MASS_STATIC_MAX_BLOCKS entries (32 KiB) that every GPU loading the
+ * library holds until the process exits.  Grids with more than
+ * FSL_MASS_STATIC_MAX_CELLS cells are rejected with FSL_EINVAL.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress with
+ * that device current); make that first call before any stream capture.
+ * Every call uses the same array, so calls whose kernels overlap on the GPU
+ * (for instance on two streams without ordering) race and give wrong sums.
+ * Asynchronous on `stream`; the result is in total_dev when the stream reaches it. */
+#define FSL_MASS_STATIC_CELLS_PER_BLOCK 65536
+#define FSL_MASS_STATIC_MAX_BLOCKS 4096
+#define FSL_MASS_STATIC_MAX_CELLS 268435456LL
+int fsl_mass_static(const fsl_params *params, const void *f, const uint8_t *flags, const float *mass,
+                    double *total_dev, void *stream);
+
 /* Which buffer (0 or 1) of fields->f holds the current PDFs. */
 int fsl_parity(const struct fsl_ctx *ctx);
 

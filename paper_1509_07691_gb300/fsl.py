@@ -63,6 +63,8 @@ _SIGNATURES = {
     "fsl_mass": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "fsl_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "fsl_step_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    "fsl_mass_static": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "fsl_parity": (ctypes.c_int, [ctypes.c_void_p]),
     "fsl_status": (ctypes.c_int, [ctypes.c_void_p]),
     "fsl_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -198,6 +200,13 @@ class Sim:
         out = (ctypes.c_int64 * 8)()
         check(lib().fsl_stats(self.ctx, out), "fsl_stats")
         return np.array(list(out), dtype=np.int64)
+
+    def mass_static(self, out: torch.Tensor) -> int:
+        """fsl_mass_static on the current state into `out` (one float64 on the
+        device); no workspace is used.  Returns the status code."""
+        return lib().fsl_mass_static(ctypes.byref(self.p), ctypes.c_void_p(self.f_current().data_ptr()),
+                                     ctypes.c_void_p(self.flags[0].data_ptr()), ctypes.c_void_p(self.mass.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_handle(self.stream)))
 
     def status(self) -> int:
         return lib().fsl_status(self.ctx)
