@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--curv", default="lsqr", choices=["lsqr", "fd", "none"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side", action="store_true", help="skip the dense-pool and precision-form measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -233,6 +234,76 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+PHASES = ["normals_plic", "lsqr_curvature", "sc_liquid", "sc_interface", "convert", "finalize"]
+
+
+def algorithmic_bytes(n_fluid, n_if, n_seg_cells):
+    """Bytes each phase must move at least, per launch (roofline table)."""
+    return {"normals_plic": 21.0 * n_if,           # phi + flag read, normal + offset written
+            "lsqr_curvature": 21.0 * n_if,         # normal + flag read, kappa written
+            "sc_liquid": 152.0 * (n_fluid - n_if) + 1.0 * n_seg_cells,  # 19 PDFs in + 19 out, flags
+            "sc_interface": 248.0 * n_if,          # own + pulled + written PDFs, m, phi, kappa, rho
+            "convert": 0.0, "finalize": 14.0 * n_if}
+
+
+def time_steps(sim, steps, stream, flush):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def phase_profile(sim, nprof, flush):
+    ph = np.zeros(len(PHASES))
+    for k in range(nprof):
+        flush.fill_(float(k))
+        ph += sim.step_profile()
+    return ph / nprof
+
+
+def roofline_of(ph, nbytes, peaks, which=None):
+    k = which if which is not None else int(np.argmax(ph))
+    name = PHASES[k]
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ach = nbytes[name] / (ph[k] * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": hbm, "frac": ach / hbm,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst; of measured)" if peaks else "fallback 6.8 TB/s",
+            "traffic": None, "algorithmic_bytes": nbytes[name], "launch_ms": float(ph[k])}
+
+
+def side_workload(F, S, name, storage, steps, stream, flush, peaks, seed):
+    """MLUPS and the liquid stream-collide roofline of one more workload."""
+    import torch
+    w = S.workload(name, seed=seed)
+    P, sim, phi0, obs = make_sim(F, w, "lsqr", storage, stream)
+    sim.step(5)
+    torch.cuda.synchronize()
+    st = sim.stats()
+    n_fluid, n_if = int(st[0] + st[1]), int(st[1])
+    m0, l0 = sim.mass_total()
+    ms = time_steps(sim, steps, stream, flush)
+    m1, l1 = sim.mass_total()
+    ph = phase_profile(sim, min(steps, 20), flush)
+    nseg_cells = n_fluid  # liquid rows are dense in this workload
+    nb = algorithmic_bytes(n_fluid, n_if, nseg_cells)
+    if storage != "f32":
+        nb["sc_liquid"] = 76.0 * (n_fluid - n_if) + 1.0 * nseg_cells
+    out = {"workload": name, "storage": storage, "fluid_cells": n_fluid, "interface_cells": n_if,
+           "mlups": n_fluid * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+           "mass_drift_rel": ((m1 + l1) - (m0 + l0)) / (m0 + l0), "mass_drift_steps": steps,
+           "phases_ms": dict(zip(PHASES, [round(float(v), 5) for v in ph])),
+           "roofline_sc_liquid": roofline_of(ph, nb, peaks, which=PHASES.index("sc_liquid"))}
+    sim.close()
+    del sim, phi0, obs
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_fsl(args):
     import torch
     ws, rank, local = dist_info()
@@ -245,6 +316,11 @@ def run_fsl(args):
     B.build()
     from paper_1509_07691_gb300 import fsl as F
     from paper_1509_07691_gb300 import synthetic as S
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
     w = S.workload(args.workload, seed=S.SEED + rank)
     stream = torch.cuda.current_stream()
     P, sim, phi0, obs = make_sim(F, w, args.curv, args.storage, stream)
@@ -255,8 +331,8 @@ def run_fsl(args):
     st = sim.stats()
     n_fluid, n_if, N = int(st[0] + st[1]), int(st[1]), sim.N
 
+    mass_start = sim.mass_total()
     # ---- timed region: K steps, each between events; L2 flushed before each
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -264,14 +340,8 @@ def run_fsl(args):
     clk = ClockSampler(local)
     time.sleep(0.15)
     t0 = time.time()
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        ev[k][0].record(stream)
-        sim.step(1)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    ms = time_steps(sim, args.steps, stream, flush)
     t1 = time.time()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
     if ws > 1:
         import torch.distributed as dist
         tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
@@ -284,15 +354,11 @@ def run_fsl(args):
         total_fluid = float(n_fluid)
     ms_per_step = ms / args.steps
     value = total_fluid * args.steps / (ms * 1e-3) / 1e6
+    mass_end = sim.mass_total()
+    drift = ((mass_end[0] + mass_end[1]) - (mass_start[0] + mass_start[1])) / (mass_start[0] + mass_start[1])
 
     # ---- per-phase device times (kernel by kernel, same state evolution)
-    nprof = min(args.steps, 50)
-    ph = np.zeros(5)
-    for k in range(nprof):
-        flush.fill_(float(k))
-        ph += sim.step_profile()
-    ph /= nprof
-    clk_prof_end = time.time()
+    ph = phase_profile(sim, min(args.steps, 50), flush)
     clk.stop()
     clocks = clk.summary(t0, t1)
 
@@ -308,7 +374,7 @@ def run_fsl(args):
     torch.cuda.synchronize()
     curv_ms = sum(a.elapsed_time(b) for a, b in cev) / len(cev)
     st2 = sim.stats()
-    n_if_now = int(st2[7])
+    n_if_now, n_fp64 = int(st2[7]), int(st2[6])
 
     # ---- mass reduction (FP64 partials) alone
     m0 = time.perf_counter()
@@ -333,26 +399,8 @@ def run_fsl(args):
            "includes": "fsl_init from pinned host fill levels (upload, types, f = w_q), graph capture, K steps, "
                        "fsl_mass read back"}
 
-    # ---- roofline of the dominant kernel
-    names = ["normals_plic", "lsqr_curvature", "stream_collide", "convert", "finalize"]
-    dom = int(np.argmax(ph))
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    bytes_per = {"stream_collide": 152.0 * n_fluid + 1.0 * N + 100.0 * n_if,
-                 "finalize": 2.0 * N + 16.0 * n_if,
-                 "normals_plic": 16.0 * n_if + 27 * 4.0 * n_if,
-                 "convert": 0.0,
-                 "lsqr_curvature": 26 * 17.0 * n_if}
-    roof = {"kernel": names[dom], "bound": "hbm", "unit": "GB/s",
-            "achieved": bytes_per[names[dom]] / (ph[dom] * 1e-3) / 1e9, "peak": hbm,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst)" if peaks else "fallback 6.8 TB/s",
-            "traffic": None, "algorithmic_bytes": bytes_per[names[dom]]}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    sc_bytes = bytes_per["stream_collide"]
+    nb = algorithmic_bytes(n_fluid, n_if, n_fluid)
+    roof = roofline_of(ph, nb, peaks)
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"f32": "f32", "f16": "f16-offset/f32", "bf16": "bf16-offset/f32"}[args.storage],
@@ -363,18 +411,28 @@ def run_fsl(args):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "fluid_cells": n_fluid, "interface_cells": n_if, "mlups_domain": N * args.steps / (ms * 1e-3) / 1e6,
             "curvature_evals_per_s": n_if_now / (curv_ms * 1e-3), "curvature_ms": curv_ms,
-            "phases_ms": dict(zip(names, [round(float(v), 5) for v in ph])),
-            "stream_collide_gbs": sc_bytes / (ph[2] * 1e-3) / 1e9,
-            "mass_reduce_ms": mass_ms, "roofline": roof, "e2e": e2e,
-            "gpu_launches": 5 * args.steps, "clocks": clocks}
+            "lsqr_fp64_cells": n_fp64,
+            "phases_ms": dict(zip(PHASES, [round(float(v), 5) for v in ph])),
+            "mass_reduce_ms": mass_ms, "mass_drift_rel": drift, "roofline": roof, "e2e": e2e,
+            "gpu_launches": 8 * args.steps, "clocks": clocks}
+    gs = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         gs = {"flags": sim2.flags_current().cpu().numpy(), "phi": sim2.phi.double().cpu().numpy()}
         sim2.curvature(F.CURV_LSQR)
         torch.cuda.synchronize()
         gs["kappa"] = sim2.kappa.double().cpu().numpy()
+    sim2.close()
+    del sim2, sim, phi0
+    torch.cuda.empty_cache()
+    if not args.no_side:
+        side_steps = min(args.steps, 200)
+        line["dense_pool"] = side_workload(F, S, "pool256", "f32", side_steps, stream, flush, peaks, S.SEED + rank)
+        line["precision_forms"] = {
+            st_: side_workload(F, S, "pool256", st_, side_steps, stream, flush, peaks, S.SEED + rank)
+            for st_ in ("f16", "bf16")}
+    if gs is not None:
         line["cpu_baseline"] = oracle_sample(w, args.cpu_seconds, gpu_state=gs)
         line["kappa_err_vs_fp64"] = line["cpu_baseline"].pop("kappa_check")
-    sim2.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

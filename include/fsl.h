@@ -174,11 +174,12 @@ int fsl_mass(struct fsl_ctx *ctx, double *total_mass, double *lost_mass);
  * Synchronising. */
 int fsl_stats(struct fsl_ctx *ctx, int64_t counts_out[8]);
 
-/* One time step like fsl_step(ctx, 1), launched kernel by kernel (no graph)
- * with CUDA events on the context's stream between its phases; ms_out[0..4]
- * receive the device time of: normals + PLIC, curvature, stream-collide,
- * conversion, finalize.  For profiling.  Synchronising. */
-int fsl_step_profile(struct fsl_ctx *ctx, float ms_out[5]);
+/* One time step like fsl_step(ctx, 1), launched kernel by kernel (no graph,
+ * phases in sequence) with CUDA events on the context's stream between its
+ * phases; ms_out[0..5] receive the device time of: normals + PLIC, curvature,
+ * liquid stream-collide, interface stream-collide, conversion, finalize.
+ * For profiling.  Synchronising. */
+int fsl_step_profile(struct fsl_ctx *ctx, float ms_out[6]);
 
 /* Total mass of a state (sum of m over interface cells plus sum of rho over
  * liquid cells) for callers that cannot allocate device memory: a host

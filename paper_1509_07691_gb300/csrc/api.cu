@@ -294,10 +294,10 @@ int fsl_step(fsl_ctx *c, int nsteps) {
     return FSL_OK;
 }
 
-int fsl_step_profile(fsl_ctx *c, float ms_out[5]) {
+int fsl_step_profile(fsl_ctx *c, float ms_out[6]) {
     if (!c || !ms_out) return FSL_EINVAL;
-    cudaEvent_t ev[6];
-    for (int k = 0; k < 6; ++k)
+    cudaEvent_t ev[7];
+    for (int k = 0; k < 7; ++k)
         if (cudaEventCreate(&ev[k]) != cudaSuccess) return FSL_ECUDA;
     const Dev d = dev_for(c, c->parity);
     cudaStream_t s = c->stream;
@@ -310,18 +310,20 @@ int fsl_step_profile(fsl_ctx *c, float ms_out[5]) {
         else if (c->p.curv_model == FSL_CURV_FD) launch_fd(d, d.kappa, s);
         else launch_zero_kappa(d, d.kappa, s);
         if (cudaEventRecord(ev[2], s) != cudaSuccess) break;
-        launch_stream_collide(d, s);
+        launch_sc_bulk(d, s);
         if (cudaEventRecord(ev[3], s) != cudaSuccess) break;
-        launch_convert(d, s);
+        launch_sc_iface(d, s);
         if (cudaEventRecord(ev[4], s) != cudaSuccess) break;
-        launch_finalize(d, s);
+        launch_convert(d, s);
         if (cudaEventRecord(ev[5], s) != cudaSuccess) break;
-        if (cudaEventSynchronize(ev[5]) != cudaSuccess) break;
-        for (int k = 0; k < 5; ++k) cudaEventElapsedTime(&ms_out[k], ev[k], ev[k + 1]);
+        launch_finalize(d, s);
+        if (cudaEventRecord(ev[6], s) != cudaSuccess) break;
+        if (cudaEventSynchronize(ev[6]) != cudaSuccess) break;
+        for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&ms_out[k], ev[k], ev[k + 1]);
         c->parity ^= 1;
         rc = FSL_OK;
     } while (0);
-    for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
+    for (int k = 0; k < 7; ++k) cudaEventDestroy(ev[k]);
     return rc;
 }
 

@@ -231,26 +231,28 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
     const int nfill = __ldcg(d.counts + C_FILL), nempty = __ldcg(d.counts + C_EMPTY);
     if (nfill + nempty == 0) return;
     const long long N = d.N;
+    // one warp per converted cell, lane q (1..18) for the neighbour x + c_q:
+    // all neighbour loads of a cell are in flight together
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const bool act = lane >= 1 && lane < Q;
+    const int q = act ? lane : 1;
     // A
-    for (int k = threadIdx.x; k < nempty; k += blockDim.x) {
+    for (int k = warp; k < nempty; k += nwarps) {
         const int i = d.empty[k];
         int x, y, z;
         cell_coords(d, i, x, y, z);
-        for (int q = 1; q < Q; ++q)
-            if (d.flags[nbr_index(d, x, y, z, cx(q), cy(q), cz(q))] & B_TOLIQ) {
-                d.flags[i] &= (uint8_t)~B_TOGAS;
-                break;
-            }
+        const bool tl = act && (d.flags[nbr_index(d, x, y, z, cx(q), cy(q), cz(q))] & B_TOLIQ);
+        if (__any_sync(0xffffffffu, tl) && lane == 0) d.flags[i] &= (uint8_t)~B_TOGAS;
     }
     __syncthreads();
     // B
-    for (int k = threadIdx.x; k < nfill + nempty; k += blockDim.x) {
+    for (int k = warp; k < nfill + nempty; k += nwarps) {
         const bool isfill = k < nfill;
         const int i = isfill ? d.fill[k] : d.empty[k - nfill];
-        if (!isfill && !(__ldcg(d.flags + i) & B_TOGAS)) continue;
+        if (!isfill && !(__ldcg(d.flags + i) & B_TOGAS)) continue;  // warp-uniform
         int x, y, z;
         cell_coords(d, i, x, y, z);
-        for (int q = 1; q < Q; ++q) {
+        if (act) {
             const int j = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
             const uint8_t fj = __ldcg(d.flags + j);
             if (isfill ? (fj & T_GAS) : (fj & T_LIQ)) {
@@ -269,17 +271,15 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
         }
     }
     __syncthreads();
-    // C: one warp per new cell; lane q (1..18) reads neighbour x + c_q
+    // C: new cells; lane q (1..18) reads neighbour x + c_q
     const int ngas = __ldcg(d.counts + C_NEWGAS), nliq = __ldcg(d.counts + C_LIQ2IF);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int k = warp; k < ngas + nliq; k += nwarps) {
         if (k < ngas) {
             const int j = d.newgas[k];
             int x, y, z;
             cell_coords(d, j, x, y, z);
             float r = 0.f, ux = 0.f, uy = 0.f, uz = 0.f, c = 0.f;
-            if (lane >= 1 && lane < Q) {
-                const int q = lane;
+            if (act) {
                 const int l = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
                 if (__ldcg(d.flags + l) & (T_LIQ | T_IF)) {
                     float jx = 0.f, jy = 0.f, jz = 0.f;
@@ -307,10 +307,10 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
             }
             const float rb = r / c, vx = ux / c, vy = uy / c, vz = uz / c;
             if (lane < Q) {
-                const int q = lane;
+                const int p = lane;
                 const float uu = 1.5f * (vx * vx + vy * vy + vz * vz);
-                const float cu = cx(q) * vx + cy(q) * vy + cz(q) * vz;
-                St::st(d.fdst, (long long)q * N + j, q, wq(q) * rb * (1.0f + 3.0f * cu + 4.5f * cu * cu - uu), d);
+                const float cu = cx(p) * vx + cy(p) * vy + cz(p) * vz;
+                St::st(d.fdst, (long long)p * N + j, p, wq(p) * rb * (1.0f + 3.0f * cu + 4.5f * cu * cu - uu), d);
             }
             if (lane == 0) {
                 d.mass[j] = 0.f;
@@ -329,22 +329,25 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
     }
     __syncthreads();
     // D
-    for (int k = threadIdx.x; k < nfill + nempty; k += blockDim.x) {
+    for (int k = warp; k < nfill + nempty; k += nwarps) {
         const bool isfill = k < nfill;
         const int i = isfill ? d.fill[k] : d.empty[k - nfill];
-        if (!isfill && !(__ldcg(d.flags + i) & B_TOGAS)) continue;
-        const float m = __ldcg(d.mass + i), r = __ldcg(d.rho + i);
-        const float mex = isfill ? m - r : m;
-        d.mass[i] = isfill ? r : 0.f;
+        if (!isfill && !(__ldcg(d.flags + i) & B_TOGAS)) continue;  // warp-uniform
         int x, y, z;
         cell_coords(d, i, x, y, z);
-        int n = 0;
-        for (int q = 1; q < Q; ++q) {
+        bool recv = false;
+        if (act) {
             const uint8_t fj = __ldcg(d.flags + nbr_index(d, x, y, z, cx(q), cy(q), cz(q)));
-            n += (((fj & T_IF) && !(fj & (B_TOLIQ | B_TOGAS))) || (fj & B_NEW)) ? 1 : 0;
+            recv = ((fj & T_IF) && !(fj & (B_TOLIQ | B_TOGAS))) || (fj & B_NEW);
         }
-        d.excess[i] = n ? mex / n : 0.f;
-        if (n == 0) atomicAdd(d.lost, (double)mex);
+        const int n = __popc(__ballot_sync(0xffffffffu, recv));
+        if (lane == 0) {
+            const float m = __ldcg(d.mass + i), r = __ldcg(d.rho + i);
+            const float mex = isfill ? m - r : m;
+            d.mass[i] = isfill ? r : 0.f;
+            d.excess[i] = n ? mex / n : 0.f;
+            if (n == 0) atomicAdd(d.lost, (double)mex);
+        }
     }
 }
 

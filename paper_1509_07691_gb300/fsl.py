@@ -181,8 +181,8 @@ class Sim:
 
     def step_profile(self) -> np.ndarray:
         """One step launched kernel by kernel; device ms of normals, curvature,
-        stream-collide, conversion, finalize."""
-        out = (ctypes.c_float * 5)()
+        liquid stream-collide, interface stream-collide, conversion, finalize."""
+        out = (ctypes.c_float * 6)()
         check(lib().fsl_step_profile(self.ctx, out), "fsl_step_profile")
         return np.array(list(out), dtype=np.float64)
 

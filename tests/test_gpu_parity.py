@@ -255,3 +255,51 @@ def test_mass_conservation_on_gpu(orc, fsl):
         assert abs((m + l) - (m0 + l0)) < 2e-5 * m0
     assert sim.status() == 0
     sim.close()
+
+
+@pytest.mark.parametrize("storage,tol_f", [(1, 1e-5), (2, 6e-5)])
+def test_single_step_parity_reduced_precision(orc, fsl, storage, tol_f):
+    """PDFs stored as 16-bit offsets f - w_q scaled by 2^8 (FP16 or BF16), collide
+    in FP32.  The oracle steps from the decoded stored state; the tolerance is
+    the rounding of the stored output: a half unit in the last place of an
+    offset of up to about 0.01 times 2^8 (2^-11 for FP16, 2^-8 for BF16,
+    divided by 2^8) plus the FP32 arithmetic."""
+    import copy
+    P, st = _developed_state(orc, 2)
+    Fp = fsl.make_params(st.phi.shape, collision=P.collision, tau=P.tau, sigma=P.sigma, theta=P.theta,
+                         storage=storage)
+    sim = fsl.Sim(Fp, phi0=st.phi.astype(np.float32))
+    sim.set_state(st.f, st.flags, st.mass, st.phi)
+    st_in = copy.copy(st)
+    st_in.f = sim.host_state()["f"]  # what the GPU holds after encoding
+    assert _guard_band(orc, P, st_in) == 0
+    ref, counts, _, _ = orc.step(P, st_in)
+    sim.step(1)
+    h = sim.host_state()
+    assert np.array_equal(h["flags"] & fsl.TYPE_MASK, ref.flags)
+    fluid = (ref.flags & 3) > 0
+    assert np.max(np.abs(h["f"][:, fluid] - ref.f[:, fluid])) <= tol_f
+    assert np.max(np.abs(h["phi"][fluid] - ref.phi[fluid])) <= TOL_F
+    iface = ref.flags == 2
+    # a cell converted from liquid gets m = rho summed over its 19 stored (rounded) PDFs
+    assert np.max(np.abs(h["mass"][iface] - ref.mass[iface])) <= max(TOL_F, 10 * tol_f)
+    sim.close()
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_reduced_precision_mass_drift_is_small(orc, fsl, storage):
+    """Rounding of the stored offsets makes the total mass drift; over 50 steps of
+    a moving droplet it stays within the storage resolution times the fluid cells."""
+    P, st = _developed_state(orc, 5, steps=1)
+    Fp = fsl.make_params(st.phi.shape, collision=P.collision, tau=P.tau, sigma=P.sigma, theta=P.theta,
+                         storage=storage)
+    sim = fsl.Sim(Fp, phi0=st.phi.astype(np.float32))
+    sim.set_state(st.f, st.flags, st.mass, st.phi)
+    m0, l0 = sim.mass_total()
+    sim.step(50)
+    m1, l1 = sim.mass_total()
+    nfluid = int(np.count_nonzero(st.flags & 3))
+    ulp = 2.0 ** -11 if storage == 1 else 2.0 ** -8
+    assert abs((m1 + l1) - (m0 + l0)) < 50 * nfluid * ulp * 0.01 * 19
+    assert sim.status() == 0
+    sim.close()
