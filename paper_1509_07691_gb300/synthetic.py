@@ -48,6 +48,18 @@ def splitmix64(seed: int, n: int) -> np.ndarray:
     return out
 
 
+def uniform_at(seed: int, index) -> np.ndarray:
+    """splitmix64 uniform in [0, 1) at counter positions `index` (the k-th
+    output of the stream started at `seed` is uniform_at(seed, k))."""
+    idx = np.asarray(index, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & MASK64) + (idx + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
 def uniform(seed: int, n: int) -> np.ndarray:
     """n doubles in [0, 1) from the top 53 bits of splitmix64."""
     return (splitmix64(seed, n) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
@@ -141,3 +153,39 @@ def field_noise(seed: int, shape, amp: float) -> np.ndarray:
 
 def gaussian_field(seed: int, shape, sd: float) -> np.ndarray:
     return (normal(seed, int(np.prod(shape))) * sd).reshape(shape)
+
+
+def mlp_sample_params(seed: int, n: int) -> dict:
+    """Shape parameters of n training stencils for the learned curvature
+    (spheres and ellipsoids, radii log-uniform in [2, 60], uniformly random
+    orientation, surface direction and sub-cell offset; 30 % bubbles).
+
+    axes (n,3) semi-axes in cells, quat (n,4) unit quaternion (w,x,y,z),
+    dir (n,3) unit direction in the body frame of the surface point that
+    passes through the middle cell, delta (n,3) that point's offset from the
+    middle cell's centre, invert (n,) 1 if the liquid is outside."""
+    u = uniform(seed, 13 * n).reshape(n, 13)
+    R = np.exp(np.log(2.0) + u[:, 0] * (np.log(60.0) - np.log(2.0)))
+    ell = u[:, 1] >= 0.5
+    axes = np.stack([R, R * np.where(ell, 0.6 + 0.4 * u[:, 2], 1.0), R * np.where(ell, 0.6 + 0.4 * u[:, 3], 1.0)], 1)
+    axes = np.maximum(axes, 2.0)
+    invert = (u[:, 4] < 0.3).astype(np.int32)
+    a, b, c = u[:, 5], 2 * np.pi * u[:, 6], 2 * np.pi * u[:, 7]
+    quat = np.stack([np.sqrt(a) * np.cos(c), np.sqrt(1 - a) * np.sin(b), np.sqrt(1 - a) * np.cos(b),
+                     np.sqrt(a) * np.sin(c)], 1)
+    zc = 2 * u[:, 8] - 1
+    ph = 2 * np.pi * u[:, 9]
+    rxy = np.sqrt(np.maximum(0.0, 1 - zc * zc))
+    d = np.stack([rxy * np.cos(ph), rxy * np.sin(ph), zc], 1)
+    delta = u[:, 10:13] - 0.5
+    return dict(axes=axes, quat=quat, dir=d, delta=delta, invert=invert)
+
+
+def mlp_init_weights(seed: int) -> dict:
+    """Initial MLP parameters: weights N(0, 1/fan_in), biases 0 (FP32)."""
+    W1 = normal(seed, 128 * 128).reshape(128, 128) / np.sqrt(125.0)
+    W1[:, 125:] = 0.0
+    W2 = normal(seed + 1, 128 * 128).reshape(128, 128) / np.sqrt(128.0)
+    w3 = normal(seed + 2, 128) / np.sqrt(128.0)
+    return dict(W1=W1.astype(np.float32), b1=np.zeros(128, np.float32), W2=W2.astype(np.float32),
+                b2=np.zeros(128, np.float32), w3=w3.astype(np.float32), b3=np.zeros(1, np.float32))
