@@ -68,7 +68,7 @@ extern "C" {
 typedef struct fsl_ctx fsl_ctx; /* opaque */
 
 enum fsl_collision { FSL_BGK = 0, FSL_TRT = 1 };
-enum fsl_curv_model { FSL_CURV_LSQR = 0, FSL_CURV_FD = 1, FSL_CURV_NONE = 2 };
+enum fsl_curv_model { FSL_CURV_LSQR = 0, FSL_CURV_FD = 1, FSL_CURV_NONE = 2, FSL_CURV_MLP = 3 };
 enum fsl_storage { FSL_F32 = 0, FSL_F16_OFS = 1, FSL_BF16_OFS = 2 };
 enum fsl_where { FSL_NONE = 0, FSL_HOST = 1, FSL_DEVICE = 2 };
 
@@ -168,11 +168,12 @@ int fsl_curvature(struct fsl_ctx *ctx, int model, float *kappa_out);
  * added in a fixed order.  Synchronising. */
 int fsl_mass(struct fsl_ctx *ctx, double *total_mass, double *lost_mass);
 
-/* counts_out[0..7]: liquid, interface, gas, obstacle cells, interface cells
+/* counts_out[0..9]: liquid, interface, gas, obstacle cells, interface cells
  * without a liquid or without a gas neighbour, liquid cells touching gas,
- * LSQR cells solved in FP64 (last curvature pass), interface list length.
- * Synchronising. */
-int fsl_stats(struct fsl_ctx *ctx, int64_t counts_out[8]);
+ * LSQR cells solved in FP64 (last curvature pass), interface list length,
+ * cells the learned curvature evaluated and cells where its value was kept
+ * (last FSL_CURV_MLP pass).  Synchronising. */
+int fsl_stats(struct fsl_ctx *ctx, int64_t counts_out[10]);
 
 /* One time step like fsl_step(ctx, 1), launched kernel by kernel (no graph,
  * phases in sequence) with CUDA events on the context's stream between its
@@ -202,6 +203,61 @@ int fsl_step_profile(struct fsl_ctx *ctx, float ms_out[6]);
 #define FSL_MASS_STATIC_MAX_CELLS 268435456LL
 int fsl_mass_static(const fsl_params *params, const void *f, const uint8_t *flags, const float *mass,
                     double *total_dev, void *stream);
+
+/* ---- Learned curvature (extension beyond the paper: an MLP estimate of the
+ * curvature from the 5x5x5 fill-level stencil, with the LSQR fit of Sec. II.C
+ * as judge and fallback) ------------------------------------------------------
+ * Network: x = bf16(2 phi - 1) over the canonical stencil (axes flipped so the
+ * Parker-Youngs normal of the middle cell is non-negative, then ordered by
+ * decreasing |n_k|; 125 values, 3 zero pads), z1 = W1 x + b1,
+ * h1 = bf16(gelu(z1)), z2 = W2 h1 + b2, y = w3 . gelu(z2) + b3 = kappa dx,
+ * gelu(x) = x Phi(x).  BF16 weights, FP32 accumulation on the tensor cores.
+ * Packed parameter block (device, fsl_mlp_param_bytes() bytes): bf16 W1[128][128]
+ * (row = hidden unit), bf16 W2[128][128], bf16 w3[128], then at byte 65792
+ * float b1[128], b2[128], b3.  FP32 master layout (fsl_mlp_master_count()
+ * floats, also used for gradients and Adam moments): W1, W2, w3, b1, b2, b3. */
+size_t fsl_mlp_param_bytes(void);
+int fsl_mlp_master_count(void);
+
+/* Training stencils: for each of n shape parameter sets (device arrays: axes
+ * [n][3] semi-axes, quat [n][4] (w,x,y,z), dir [n][3] body-frame direction of
+ * the surface point placed at the middle cell, delta [n][3] its offset from
+ * the middle cell's centre, invert [n] 1 = liquid outside), the 5x5x5 fill
+ * levels by sub^3 sub-sampling, Gaussian noise of s.d. `noise` on partially
+ * filled cells (splitmix64 at counters 2k, 2k+1 for stencil cell k of sample s,
+ * k = 125 s + cell, Box-Muller; clipped to [0, 1]), written as canonical BF16
+ * rows X [n][128], and the target: mean curvature at the surface point nearest
+ * the middle cell's centre (negative for liquid outside).  Asynchronous. */
+int fsl_mlp_stencils(int n, const float *axes, const float *quat, const float *dir, const float *delta,
+                     const int32_t *invert, int sub, float noise, uint64_t noise_seed, void *X, float *target,
+                     void *stream);
+
+/* y [n] = network(X [n][128] bf16); with z1, z2 (each [n][128] floats) the
+ * pre-activations are kept for the backward pass.  Asynchronous. */
+int fsl_mlp_forward(const void *params, const void *X, int n, float *y, float *z1, float *z2, void *stream);
+
+/* Bytes of workspace the training calls need for a batch of n. */
+size_t fsl_mlp_train_workspace(int n);
+
+/* Gradients (master layout) of loss = (1/n) sum w (y - t)^2, w = 1/(t^2 + 7e-5),
+ * and the loss itself (one float, device; may be NULL).  Asynchronous. */
+int fsl_mlp_gradients(const void *params, const void *X, const float *target, int n, float *grad, float *loss_dev,
+                      void *workspace, void *stream);
+
+/* One training step: gradients, then Adam (beta 0.9 / 0.999, eps 1e-8, bias
+ * correction with step counted from 1) on the FP32 master weights, and the
+ * packed BF16 parameters refreshed from them.  Asynchronous. */
+int fsl_mlp_train_step(void *params, float *master, float *m, float *v, const void *X, const float *target, int n,
+                       float lr, int step, float *loss_dev, void *workspace, void *stream);
+
+/* Packed parameters from FP32 master weights (BF16 rounding).  Asynchronous. */
+int fsl_mlp_pack(const float *master, void *params, void *stream);
+
+/* Use the network in the context (curvature model FSL_CURV_MLP): after the LSQR
+ * fit of every interface cell, the network's value replaces it where
+ * |kappa_mlp - kappa_lsqr| <= fallback_rel |kappa_lsqr| and the stencil holds no
+ * obstacle cell.  The parameters stay caller-owned.  Resets recorded graphs. */
+int fsl_mlp_attach(struct fsl_ctx *ctx, const void *params, double fallback_rel);
 
 /* Which buffer (0 or 1) of fields->f holds the current PDFs. */
 int fsl_parity(const struct fsl_ctx *ctx);

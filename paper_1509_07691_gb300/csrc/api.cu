@@ -70,7 +70,7 @@ bool valid_params(const fsl_params *p) {
     if (N >= 2147483647.0) return false;  // cell indices are int32 in the lists
     if (p->nx > 65535 * 256 || p->ny > 65535 || p->nz > 65535) return false;
     if (p->collision != FSL_BGK && p->collision != FSL_TRT) return false;
-    if (p->curv_model < FSL_CURV_LSQR || p->curv_model > FSL_CURV_NONE) return false;
+    if (p->curv_model < FSL_CURV_LSQR || p->curv_model > FSL_CURV_MLP) return false;
     if (p->storage < FSL_F32 || p->storage > FSL_BF16_OFS) return false;
     if (p->storage != FSL_F32 && (p->storage_shift < 0 || p->storage_shift > 24)) return false;
     if (!(p->tau > 0.5) || !isfinite(p->tau)) return false;
@@ -159,9 +159,10 @@ Dev dev_for(const fsl_ctx *c, int parity) {
 // enqueue the curvature of the current state into kappa_out
 void enqueue_curvature(const Dev &d, int model, float *kappa_out, cudaStream_t s) {
     launch_normals(d, s);
-    if (model == FSL_CURV_LSQR) launch_lsqr(d, kappa_out, s);
+    if (model == FSL_CURV_LSQR || model == FSL_CURV_MLP) launch_lsqr(d, kappa_out, s);
     else if (model == FSL_CURV_FD) launch_fd(d, kappa_out, s);
     else launch_zero_kappa(d, kappa_out, s);
+    if (model == FSL_CURV_MLP) launch_mlp_curv(d, kappa_out, s);
 }
 
 // One time step from parity p (see fsl_step), recorded as a graph with two
@@ -283,6 +284,7 @@ int fsl_refresh(fsl_ctx *c) {
 
 int fsl_step(fsl_ctx *c, int nsteps) {
     if (!c || nsteps < 0) return FSL_EINVAL;
+    if (c->p.curv_model == FSL_CURV_MLP && !c->base.mlp_params) return FSL_EINVAL;
     for (int s = 0; s < nsteps; ++s) {
         if (!c->graph[c->parity]) {
             const int rc = record_graph(c, c->parity);
@@ -306,9 +308,10 @@ int fsl_step_profile(fsl_ctx *c, float ms_out[6]) {
         if (cudaEventRecord(ev[0], s) != cudaSuccess) break;
         launch_normals(d, s);
         if (cudaEventRecord(ev[1], s) != cudaSuccess) break;
-        if (c->p.curv_model == FSL_CURV_LSQR) launch_lsqr(d, d.kappa, s);
+        if (c->p.curv_model == FSL_CURV_LSQR || c->p.curv_model == FSL_CURV_MLP) launch_lsqr(d, d.kappa, s);
         else if (c->p.curv_model == FSL_CURV_FD) launch_fd(d, d.kappa, s);
         else launch_zero_kappa(d, d.kappa, s);
+        if (c->p.curv_model == FSL_CURV_MLP) launch_mlp_curv(d, d.kappa, s);
         if (cudaEventRecord(ev[2], s) != cudaSuccess) break;
         launch_sc_bulk(d, s);
         if (cudaEventRecord(ev[3], s) != cudaSuccess) break;
@@ -328,7 +331,8 @@ int fsl_step_profile(fsl_ctx *c, float ms_out[6]) {
 }
 
 int fsl_curvature(fsl_ctx *c, int model, float *kappa_out) {
-    if (!c || !kappa_out || model < FSL_CURV_LSQR || model > FSL_CURV_NONE) return FSL_EINVAL;
+    if (!c || !kappa_out || model < FSL_CURV_LSQR || model > FSL_CURV_MLP) return FSL_EINVAL;
+    if (model == FSL_CURV_MLP && !c->base.mlp_params) return FSL_EINVAL;
     const Dev d = dev_for(c, c->parity);
     enqueue_curvature(d, model, kappa_out, c->stream);
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
@@ -345,7 +349,20 @@ int fsl_mass(fsl_ctx *c, double *total_mass, double *lost_mass) {
     return FSL_OK;
 }
 
-int fsl_stats(fsl_ctx *c, int64_t counts_out[8]) {
+int fsl_mlp_attach(fsl_ctx *c, const void *params, double fallback_rel) {
+    if (!c || !params || !(fallback_rel >= 0.0)) return FSL_EINVAL;
+    c->base.mlp_params = static_cast<const uint8_t *>(params);
+    c->base.mlp_rel = (float)fallback_rel;
+    // recorded graphs hold the old parameters
+    for (int k = 0; k < 2; ++k)
+        if (c->graph[k]) {
+            cudaGraphExecDestroy(c->graph[k]);
+            c->graph[k] = nullptr;
+        }
+    return FSL_OK;
+}
+
+int fsl_stats(fsl_ctx *c, int64_t counts_out[10]) {
     if (!c || !counts_out) return FSL_EINVAL;
     const Dev d = dev_for(c, c->parity);
     CK(cudaMemsetAsync(d.stats, 0, 16 * sizeof(long long), c->stream));
@@ -357,6 +374,8 @@ int fsl_stats(fsl_ctx *c, int64_t counts_out[8]) {
     for (int k = 0; k < 6; ++k) counts_out[k] = c->host_stats[k];
     counts_out[6] = cnt[C_FP64];
     counts_out[7] = cnt[C_IF0 + c->parity];
+    counts_out[8] = cnt[C_MLP];
+    counts_out[9] = cnt[C_MLPKEEP];
     return FSL_OK;
 }
 

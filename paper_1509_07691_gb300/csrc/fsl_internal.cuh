@@ -48,7 +48,7 @@ enum : uint8_t {
 // device counters in the workspace: interface-list lengths of the two list
 // buffers, conversion lists, FP64 LSQR re-solves, active segments
 enum { C_IF0 = 0, C_IF1 = 1, C_FILL = 2, C_EMPTY = 3, C_NEWGAS = 4, C_LIQ2IF = 5, C_FP64 = 6, C_SEG = 7, C_SLOW = 8,
-       C_NCOUNT = 16 };
+       C_MLP = 9, C_MLPKEEP = 10, C_NCOUNT = 16 };
 
 // the grid is walked in x-row segments of SEG cells (one warp each); a
 // segment is active while it holds a liquid or interface cell
@@ -87,6 +87,9 @@ struct Dev {
     float scale, inv_scale;  // 16-bit offset storage
     float fp64_cond;
     double cos_theta_d, sin_theta_d;
+    // learned curvature (FSL_CURV_MLP): packed parameters, judge tolerance
+    const uint8_t *mlp_params;
+    float mlp_rel;
 };
 
 // ---- PDF storage -----------------------------------------------------------
@@ -231,6 +234,7 @@ void launch_normals(const Dev &d, cudaStream_t s);
 void launch_lsqr(const Dev &d, float *kappa_out, cudaStream_t s);
 void launch_fd(const Dev &d, float *kappa_out, cudaStream_t s);
 void launch_zero_kappa(const Dev &d, float *kappa_out, cudaStream_t s);
+void launch_mlp_curv(const Dev &d, float *kappa_out, cudaStream_t s);
 
 int max_partials();
 // blocks of `block` threads of `kernel` that are resident on the whole GPU at once

@@ -161,8 +161,9 @@ __global__ void __launch_bounds__(LIST_THREADS) k_normals(Dev d) {
     int cnt[1];
     block_counts<1>(d.counts, {d.cif}, cnt);
     const int n = cnt[0];
+    if (blockIdx.x == 0 && threadIdx.x == 8) d.counts[d.cif_next] = 0;
     if (blockIdx.x == 0 && threadIdx.x < 8) {
-        const int zero[8] = {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF, C_SLOW, C_FP64, d.cif_next, d.cif_next};
+        const int zero[8] = {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF, C_SLOW, C_FP64, C_MLP, C_MLPKEEP};
         d.counts[zero[threadIdx.x]] = 0;
     }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfsl.so")
 OK, EINVAL, ECUDA, ECAPACITY, ETIMEOUT, ENAN, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 LIQUID, INTERFACE, GAS, OBSTACLE, TYPE_MASK, NEAR_OBSTACLE = 1, 2, 4, 8, 15, 16
 BGK, TRT = 0, 1
-CURV_LSQR, CURV_FD, CURV_NONE = 0, 1, 2
+CURV_LSQR, CURV_FD, CURV_NONE, CURV_MLP = 0, 1, 2, 3
 F32, F16_OFS, BF16_OFS = 0, 1, 2
 WHERE_NONE, WHERE_HOST, WHERE_DEVICE = 0, 1, 2
 GEOMETRY_KINDS = {"sphere": 0, "mode2": 1, "cap": 2, "two_spheres": 3, "pool": 4, "plane": 5}
@@ -65,6 +65,18 @@ _SIGNATURES = {
     "fsl_step_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     "fsl_mass_static": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "fsl_mlp_param_bytes": (ctypes.c_size_t, []),
+    "fsl_mlp_master_count": (ctypes.c_int, []),
+    "fsl_mlp_stencils": (ctypes.c_int, [ctypes.c_int] + [ctypes.c_void_p] * 5 + [ctypes.c_int, ctypes.c_float,
+                                                                                   ctypes.c_uint64] + [ctypes.c_void_p] * 3),
+    "fsl_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),
+    "fsl_mlp_train_workspace": (ctypes.c_size_t, [ctypes.c_int]),
+    "fsl_mlp_gradients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] +
+                          [ctypes.c_void_p] * 4),
+    "fsl_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_int, ctypes.c_float, ctypes.c_int] +
+                           [ctypes.c_void_p] * 3),
+    "fsl_mlp_pack": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "fsl_mlp_attach": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     "fsl_parity": (ctypes.c_int, [ctypes.c_void_p]),
     "fsl_status": (ctypes.c_int, [ctypes.c_void_p]),
     "fsl_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -197,7 +209,7 @@ class Sim:
         return m.value, lost.value
 
     def stats(self) -> np.ndarray:
-        out = (ctypes.c_int64 * 8)()
+        out = (ctypes.c_int64 * 10)()
         check(lib().fsl_stats(self.ctx, out), "fsl_stats")
         return np.array(list(out), dtype=np.int64)
 
@@ -207,6 +219,11 @@ class Sim:
         return lib().fsl_mass_static(ctypes.byref(self.p), ctypes.c_void_p(self.f_current().data_ptr()),
                                      ctypes.c_void_p(self.flags[0].data_ptr()), ctypes.c_void_p(self.mass.data_ptr()),
                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_handle(self.stream)))
+
+    def attach_mlp(self, net: "Mlp", fallback_rel: float = 0.05):
+        self._mlp = net
+        check(lib().fsl_mlp_attach(self.ctx, ctypes.c_void_p(net.params.data_ptr()), float(fallback_rel)),
+              "fsl_mlp_attach")
 
     def status(self) -> int:
         return lib().fsl_status(self.ctx)
@@ -265,3 +282,76 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+class Mlp:
+    """Learned curvature network: packed BF16 parameters and FP32 master weights
+    with Adam moments, all torch device tensors."""
+
+    def __init__(self, init: dict, device="cuda", stream=None):
+        self.device = torch.device(device)
+        self.stream = stream
+        cnt = lib().fsl_mlp_master_count()
+        master = np.concatenate([np.asarray(init[k], np.float32).ravel() for k in ("W1", "W2", "w3", "b1", "b2", "b3")])
+        assert master.size == cnt
+        self.master = torch.from_numpy(master).to(self.device)
+        self.m = torch.zeros(cnt, dtype=torch.float32, device=self.device)
+        self.v = torch.zeros(cnt, dtype=torch.float32, device=self.device)
+        self.params = torch.zeros(lib().fsl_mlp_param_bytes(), dtype=torch.uint8, device=self.device)
+        self.step = 0
+        self._ws = None
+        check(lib().fsl_mlp_pack(_ptr(self.master), _ptr(self.params), _stream_handle(stream)), "fsl_mlp_pack")
+
+    def _workspace(self, n):
+        need = lib().fsl_mlp_train_workspace(int(n))
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def forward(self, X, keep=False):
+        n = X.shape[0]
+        y = torch.empty(n, dtype=torch.float32, device=self.device)
+        z1 = torch.empty((n, 128), dtype=torch.float32, device=self.device) if keep else None
+        z2 = torch.empty((n, 128), dtype=torch.float32, device=self.device) if keep else None
+        check(lib().fsl_mlp_forward(_ptr(self.params), _ptr(X), n, _ptr(y), _ptr(z1), _ptr(z2),
+                                    _stream_handle(self.stream)), "fsl_mlp_forward")
+        return (y, z1, z2) if keep else y
+
+    def gradients(self, X, target):
+        n = X.shape[0]
+        g = torch.empty(self.master.numel(), dtype=torch.float32, device=self.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        check(lib().fsl_mlp_gradients(_ptr(self.params), _ptr(X), _ptr(target), n, _ptr(g), _ptr(loss),
+                                      _ptr(self._workspace(n)), _stream_handle(self.stream)), "fsl_mlp_gradients")
+        return g, loss
+
+    def train_step(self, X, target, lr, loss_out=None):
+        self.step += 1
+        n = X.shape[0]
+        check(lib().fsl_mlp_train_step(_ptr(self.params), _ptr(self.master), _ptr(self.m), _ptr(self.v), _ptr(X),
+                                       _ptr(target), n, float(lr), self.step, _ptr(loss_out),
+                                       _ptr(self._workspace(n)), _stream_handle(self.stream)), "fsl_mlp_train_step")
+
+    def master_dict(self):
+        a = self.master.cpu().numpy()
+        o = [0, 16384, 32768, 32896, 33024, 33152, 33153]
+        shp = [(128, 128), (128, 128), (128,), (128,), (128,), (1,)]
+        return {k: a[o[i]:o[i + 1]].reshape(shp[i]) for i, k in enumerate(("W1", "W2", "w3", "b1", "b2", "b3"))}
+
+
+def mlp_stencils(params: dict, sub=8, noise=1e-3, noise_seed=0, device="cuda", stream=None):
+    """Training stencils on the GPU from synthetic.mlp_sample_params(...)."""
+    n = int(params["axes"].shape[0])
+    dev = torch.device(device)
+    t = {k: torch.from_numpy(np.ascontiguousarray(params[k], np.float32)).to(dev) for k in ("axes", "quat", "dir", "delta")}
+    inv = torch.from_numpy(np.ascontiguousarray(params["invert"], np.int32)).to(dev)
+    X = torch.empty((n, 128), dtype=torch.bfloat16, device=dev)
+    target = torch.empty(n, dtype=torch.float32, device=dev)
+    check(lib().fsl_mlp_stencils(n, _ptr(t["axes"]), _ptr(t["quat"]), _ptr(t["dir"]), _ptr(t["delta"]), _ptr(inv),
+                                 int(sub), float(noise), int(noise_seed), _ptr(X), _ptr(target),
+                                 _stream_handle(stream)), "fsl_mlp_stencils")
+    return X, target
