@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-side", action="store_true", help="skip the dense-pool and precision-form measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--mlp-train", type=int, default=10_000_000, help="training stencils of the learned curvature")
+    ap.add_argument("--mlp-epochs", type=int, default=2)
     return ap.parse_args()
 
 
@@ -212,6 +214,28 @@ def kappa_error(orc, gs, w, n_sample=300, half=3):
             "definition": "|k_gpu - k_fp64| / max(|k_fp64|, 1/L), FP64 oracle LSQR on the same FP32 fill levels"}
 
 
+def heldout_errors(held):
+    """Relative curvature error of the network and of the FP64 LSQR fit on the
+    same noisy held-out droplet stencils (oracle LSQR on each 5^3 stencil)."""
+    import oracle as orc
+    import oracle.mlp as M
+    q, truth, ym = held["params"], held["truth"], held["mlp"]
+    P = orc.params((5, 5, 5), curv_model=0)
+    kl = []
+    for k in range(len(truth)):
+        s = M.stencil_fill(q["axes"][k], q["quat"][k], M.shape_centre(q["axes"][k], q["quat"][k], q["dir"][k],
+                                                                      q["delta"][k]), 0, 8)
+        nz = M.noise_normal(held["noise_seed"], k * 125 + np.arange(125)).reshape(5, 5, 5) * 1e-3
+        s = np.where((s > 0) & (s < 1), np.clip(s + nz, 0.0, 1.0), s)
+        st = orc.init_state(P, np.transpose(s, (2, 1, 0)).copy())
+        kk, _, _ = orc.curvature(P, st.flags, st.phi)
+        kl.append(kk[2, 2, 2])
+    kl = np.array(kl)
+    return {"stencils": int(len(truth)), "radii": "4..48 cells, droplets, noise 1e-3",
+            "network_mean_rel": float(np.mean(np.abs(ym - truth) / np.abs(truth))),
+            "lsqr_fp64_mean_rel": float(np.mean(np.abs(kl - truth) / np.abs(truth)))}
+
+
 # ---------------------------------------------------------------- main legs
 def run_reference(args):
     ws, rank, _ = dist_info()
@@ -300,6 +324,81 @@ def side_workload(F, S, name, storage, steps, stream, flush, peaks, seed):
            "roofline_sc_liquid": roofline_of(ph, nb, peaks, which=PHASES.index("sc_liquid"))}
     sim.close()
     del sim, phi0, obs
+    torch.cuda.empty_cache()
+    return out
+
+
+def learned_curvature(F, S, stream, flush, peaks, seed, n_train, epochs, steps):
+    """Config-5 form: train the network on GPU-made stencils, then run the
+    384^3 two-droplet coalescence with FSL_CURV_MLP (LSQR judge, 5 %)."""
+    import torch
+    out = {}
+    p = S.mlp_sample_params(seed, n_train)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, target = F.mlp_stencils(p, sub=8, noise=1e-3, noise_seed=seed + 1)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    net = F.Mlp(S.mlp_init_weights(seed + 2))
+    B = 4096
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nsteps = 0
+    for ep in range(epochs):
+        perm = torch.randperm(n_train, device="cuda", generator=gen)
+        lr = 2e-3 * (0.5 ** ep)
+        for b in range(0, n_train - B + 1, B):
+            idx = perm[b:b + B]
+            net.train_step(X[idx], target[idx], lr, loss_out=loss)
+            nsteps += 1
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    out["training"] = {"stencils": n_train, "sub_samples": 8, "noise": 1e-3, "stencils_per_s": n_train / gen_s,
+                       "epochs": epochs, "batch": B, "steps": nsteps, "samples_per_s": nsteps * B / train_s,
+                       "final_batch_loss": float(loss.item()),
+                       "flops_per_sample": 3 * 2 * (128 * 128 * 2 + 128)}
+    del X, target
+    torch.cuda.empty_cache()
+    # held-out stencils for the kappa error (network here; LSQR in the CPU leg)
+    nt = 256
+    q = S.mlp_sample_params(seed + 3, nt)
+    R = np.exp(np.log(4.0) + S.uniform(seed + 4, nt) * (np.log(48.0) - np.log(4.0)))
+    q["axes"] = np.stack([R, R, R], 1)
+    q["invert"] = np.zeros(nt, np.int32)
+    Xt, tt = F.mlp_stencils(q, sub=8, noise=1e-3, noise_seed=seed + 5)
+    yt = net.forward(Xt).cpu().numpy()
+    out["heldout"] = {"params": q, "noise_seed": seed + 5, "truth": tt.cpu().numpy(), "mlp": yt}
+    # inference inside FSLBM
+    w = S.workload("coalescence384", seed=seed)
+    P = F.make_params(w["shape"], collision=F.BGK, curv_model=F.CURV_MLP, tau=w["tau"], sigma=w["sigma"],
+                      theta=w["theta"])
+    phi0 = torch.zeros(w["shape"], dtype=torch.float32, device="cuda")
+    F.fill_geometry(P, F.make_geometry(w["geometry"]["kind"], **geometry_kwargs(w["geometry"])), phi0, stream)
+    sim = F.Sim(P, phi0=phi0, stream=stream)
+    sim.attach_mlp(net, 0.05)
+    sim.step(5)
+    torch.cuda.synchronize()
+    st = sim.stats()
+    n_fluid, n_if = int(st[0] + st[1]), int(st[1])
+    ms = time_steps(sim, steps, stream, flush)
+    st = sim.stats()
+    kap = torch.empty_like(sim.kappa)
+    cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+    for a, b in cev:
+        flush.fill_(1.0)
+        a.record(stream)
+        sim.curvature(F.CURV_MLP, kap)
+        b.record(stream)
+    torch.cuda.synchronize()
+    cm = sum(a.elapsed_time(b) for a, b in cev) / len(cev)
+    out["inference"] = {"workload": "coalescence384", "grid": list(w["shape"][::-1]), "fluid_cells": n_fluid,
+                        "interface_cells": n_if, "mlups": n_fluid * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+                        "mlp_cells_last_step": int(st[8]), "kept_fraction": float(st[9]) / max(1, int(st[8])),
+                        "curvature_ms_lsqr_plus_mlp": cm, "curvature_evals_per_s": n_if / (cm * 1e-3)}
+    sim.close()
+    del sim, phi0
     torch.cuda.empty_cache()
     return out
 
@@ -430,9 +529,15 @@ def run_fsl(args):
         line["precision_forms"] = {
             st_: side_workload(F, S, "pool256", st_, side_steps, stream, flush, peaks, S.SEED + rank)
             for st_ in ("f16", "bf16")}
+        lc = learned_curvature(F, S, stream, flush, peaks, S.SEED + rank, args.mlp_train, args.mlp_epochs,
+                               min(args.steps, 100))
+        held = lc.pop("heldout")
+        line["learned_curvature"] = lc
     if gs is not None:
         line["cpu_baseline"] = oracle_sample(w, args.cpu_seconds, gpu_state=gs)
         line["kappa_err_vs_fp64"] = line["cpu_baseline"].pop("kappa_check")
+        if not args.no_side:
+            line["learned_curvature"]["heldout_kappa_rel_err"] = heldout_errors(held)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
