@@ -290,14 +290,34 @@ def phase_profile(sim, nprof, flush):
     return ph / nprof
 
 
-def roofline_of(ph, nbytes, peaks, which=None):
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu capture (profiles/ncu_traffic.json),
+    or None when the kernel's source changed since the capture."""
+    import hashlib
+    try:
+        data = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    except (OSError, ValueError):
+        return None
+    for e in data.get("entries", []):
+        if e["kernel"] != kernel or e["workload"] != workload:
+            continue
+        h = hashlib.sha256()
+        for f in e["source_files"]:
+            h.update(open(os.path.join(ROOT, "paper_1509_07691_gb300", "csrc", f), "rb").read())
+        return float(e["bytes_per_launch"]) if h.hexdigest()[:16] == e["source_sha"] else None
+    return None
+
+
+def roofline_of(ph, nbytes, peaks, which=None, workload=None):
     k = which if which is not None else int(np.argmax(ph))
     name = PHASES[k]
     hbm = peaks.get("hbm_gbs", 6800.0)
     ach = nbytes[name] / (ph[k] * 1e-3) / 1e9
     return {"kernel": name, "bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": hbm, "frac": ach / hbm,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst; of measured)" if peaks else "fallback 6.8 TB/s",
-            "traffic": None, "algorithmic_bytes": nbytes[name], "launch_ms": float(ph[k])}
+            "traffic": measured_traffic(name, workload) if workload else None,
+            "traffic_source": "profiles/ncu_traffic.json (ncu dram bytes per launch)",
+            "algorithmic_bytes": nbytes[name], "launch_ms": float(ph[k])}
 
 
 def side_workload(F, S, name, storage, steps, stream, flush, peaks, seed):
@@ -321,7 +341,8 @@ def side_workload(F, S, name, storage, steps, stream, flush, peaks, seed):
            "mlups": n_fluid * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
            "mass_drift_rel": ((m1 + l1) - (m0 + l0)) / (m0 + l0), "mass_drift_steps": steps,
            "phases_ms": dict(zip(PHASES, [round(float(v), 5) for v in ph])),
-           "roofline_sc_liquid": roofline_of(ph, nb, peaks, which=PHASES.index("sc_liquid"))}
+           "roofline_sc_liquid": roofline_of(ph, nb, peaks, which=PHASES.index("sc_liquid"),
+                                             workload=name if storage == "f32" else None)}
     sim.close()
     del sim, phi0, obs
     torch.cuda.empty_cache()
@@ -499,7 +520,7 @@ def run_fsl(args):
                        "fsl_mass read back"}
 
     nb = algorithmic_bytes(n_fluid, n_if, n_fluid)
-    roof = roofline_of(ph, nb, peaks)
+    roof = roofline_of(ph, nb, peaks, workload=args.workload if args.storage == "f32" else None)
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"f32": "f32", "f16": "f16-offset/f32", "bf16": "bf16-offset/f32"}[args.storage],
