@@ -58,7 +58,8 @@ class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("collision", ctypes.c_int), ("curv_model", ctypes.c_int), ("literal_phi", ctypes.c_int),
                 ("tau", ctypes.c_double), ("magic", ctypes.c_double), ("sigma", ctypes.c_double),
-                ("p_gas", ctypes.c_double), ("theta", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("p_gas", ctypes.c_double), ("theta", ctypes.c_double), ("eps", ctypes.c_double),
+                ("frozen", ctypes.c_int)]
 
 
 class Geom(ctypes.Structure):
@@ -130,10 +131,11 @@ def lattice():
 
 
 def params(shape, collision=0, curv_model=0, tau=1.0, magic=3.0 / 16.0, sigma=0.0, p_gas=1.0 / 3.0,
-           theta=np.pi / 2, eps=1e-3, literal_phi=0) -> Params:
-    """shape = (nz, ny, nx) of the numpy arrays (x fastest)."""
+           theta=np.pi / 2, eps=1e-3, literal_phi=0, frozen=0) -> Params:
+    """shape = (nz, ny, nx) of the numpy arrays (x fastest).  frozen = 1: cell
+    types frozen (no conversion test), as in the adjoint windows."""
     nz, ny, nx = shape
-    return Params(nx, ny, nz, collision, curv_model, literal_phi, tau, magic, sigma, p_gas, theta, eps)
+    return Params(nx, ny, nz, collision, curv_model, literal_phi, tau, magic, sigma, p_gas, theta, eps, frozen)
 
 
 def feq(q, rho, u):

@@ -50,6 +50,7 @@ typedef struct {
     double p_gas;    /* gas pressure p_g */
     double theta;    /* equilibrium contact angle theta_eq in radians */
     double eps;      /* conversion threshold */
+    int frozen;      /* 1 = cell types frozen: no conversion test, no excess mass */
 } orc_params;
 
 typedef struct {
@@ -789,8 +790,13 @@ void orc_curvature(const orc_params *P, const uint8_t *flags, const double *phi,
  * from gas get f = feq(mean rho, mean u) of their fluid neighbours and m = 0,
  * liquid neighbours of emptied cells become interface with m = rho, excess
  * mass is shared equally by the interface neighbours after conversion).
+ * With P->frozen the conversion test is skipped: no cell changes type, and
+ * the step is a smooth function of (f', m, phi, sigma, theta) (the reading
+ * of the adjoint windows; central differences of it give the FP64 reference
+ * gradient).
  * Pinned: rest state, uniform flow, shear-wave decay, exact mass
- * conservation, invariants; the conversion readings are otherwise unpinned. */
+ * conservation, invariants; the conversion readings are otherwise unpinned;
+ * the frozen step equals the plain step where nothing converts. */
 void orc_step(const orc_params *P, const double *fin, double *fout, uint8_t *flags, double *mass, double *phi,
               const double *kappa, const double *normal4, double *rho, double *lost, long *counts) {
     long N = ncell(P);
@@ -857,6 +863,7 @@ void orc_step(const orc_params *P, const double *fin, double *fout, uint8_t *fla
             } else {
                 mnew[x] = mass[x] + dm;
             }
+            if (P->frozen) continue; /* types frozen: m and phi leave [0, rho] freely */
             if (mnew[x] > (1.0 + P->eps) * r) conv[x] = 1;
             else if (mnew[x] < -P->eps * r) conv[x] = 2;
         }
