@@ -259,6 +259,62 @@ int fsl_mlp_pack(const float *master, void *params, void *stream);
  * obstacle cell.  The parameters stay caller-owned.  Resets recorded graphs. */
 int fsl_mlp_attach(struct fsl_ctx *ctx, const void *params, double fallback_rel);
 
+/* ---- Adjoint windows (extension beyond the paper: gradients of a loss on the
+ * fill level with respect to sigma and theta, through a window of steps with
+ * frozen cell types) -----------------------------------------------------------
+ * With the types frozen (no conversion test, no excess mass; the interface
+ * list stays that of the window's first step) the step is a smooth map of the
+ * state (f', m, phi) and of sigma (the Laplace term 2 sigma kappa of the
+ * free-boundary condition, Eq. reconstruct) and theta (the contact normal of
+ * the LSQR fit, Sec. II.C, Eq. contactNormal).  fsl_window_forward runs W such
+ * steps and keeps a checkpoint of (f', m, phi) every K steps;
+ * fsl_window_adjoint takes dL/dphi at the end of the window and returns
+ * dL/dsigma and dL/dtheta (theta in radians) by the exact reverse of the
+ * FP32 step: each K-step segment is recomputed from its checkpoint (all K
+ * states kept), then reversed step by step.  Needs FSL_F32 storage, the LSQR
+ * curvature (or FSL_CURV_NONE) and a grid of at least 7 cells per axis.
+ *
+ * Adjoint workspace: caller-owned device memory of
+ * fsl_adjoint_workspace_size(params, W, K, max_interface) bytes (256-byte
+ * aligned); max_interface bounds the interface cells of the window (one
+ * curvature Jacobian row of FSL_JAC_STRIDE floats each).  The workspace must
+ * stay untouched between the forward and the adjoint call. */
+#define FSL_JAC_STRIDE 344 /* 7x7x7 window slots (dz+3)*49+(dy+3)*7+(dx+3), then theta */
+size_t fsl_adjoint_workspace_size(const fsl_params *params, int window, int ckpt_every, int max_interface);
+
+/* Change sigma and theta (radians) of the context.  Resets recorded graphs and
+ * ends the current adjoint window. */
+int fsl_set_surface(struct fsl_ctx *ctx, double sigma, double theta);
+
+/* W steps with frozen cell types from the current state, checkpoints every K
+ * steps into the adjoint workspace.  Afterwards the context holds the state
+ * of step W; fsl_step continues from it (conversions resume).  Reads the
+ * interface count once (synchronising); FSL_ECAPACITY if it exceeds
+ * max_interface (nothing advanced). */
+int fsl_window_forward(struct fsl_ctx *ctx, int window, int ckpt_every, int max_interface, void *adj_workspace,
+                       size_t adj_bytes);
+
+/* Reverse pass over the last window.  dL_dphi (device, N floats): dL/dphi at
+ * the window's end; only interface entries are read (phi is constant at other
+ * cells).  dL_dsigma, dL_dtheta: host doubles.  Optional device outputs
+ * (NULL to skip), all at the window's start with phi, m and f' taken as
+ * independent inputs: dL_dphi0 and dL_dmass0 (N floats, interface entries,
+ * 0 elsewhere), dL_df0 (19 N floats, fluid cells, 0 elsewhere).
+ * Synchronising.  The window stays valid (the call may be repeated with
+ * another dL_dphi) until the context steps, refreshes or changes sigma/theta. */
+int fsl_window_adjoint(struct fsl_ctx *ctx, const float *dL_dphi, double *dL_dsigma, double *dL_dtheta,
+                       float *dL_dphi0, float *dL_dmass0, float *dL_df0);
+
+/* Curvature Jacobian of the current state: for each interface cell x (order
+ * in cells_out), row jac_out[k*FSL_JAC_STRIDE ...] = dkappa_x/dphi_y over the
+ * interface cells y of the 7x7x7 window around x (slots of other cells are
+ * not written) and dkappa_x/dtheta last; kappa_out[k] = kappa_x of the same
+ * evaluation (forward-mode dual numbers through the LSQR fit).  Device
+ * outputs of max_interface rows; adj_workspace as for a window of 1 step.
+ * *n_out = interface cells (synchronising; FSL_ECAPACITY above max_interface). */
+int fsl_kappa_jacobian(struct fsl_ctx *ctx, void *adj_workspace, size_t adj_bytes, int max_interface, float *jac_out,
+                       int32_t *cells_out, float *kappa_out, int *n_out);
+
 /* Which buffer (0 or 1) of fields->f holds the current PDFs. */
 int fsl_parity(const struct fsl_ctx *ctx);
 

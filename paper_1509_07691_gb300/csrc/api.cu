@@ -6,6 +6,7 @@
 
 #include <new>
 
+#include "adjoint.cuh"
 #include "fsl_internal.cuh"
 
 using namespace fslk;
@@ -21,8 +22,12 @@ struct fsl_ctx {
     Dev base;                // pointers and parameters common to both parities
     cudaGraphExec_t graph[2];
     double *mass_out;        // 2 doubles in the workspace
-    double *host_mass;       // pinned, 2 doubles
+    double *host_mass;       // pinned, 4 doubles (mass, lost; dL/dsigma, dL/dtheta)
     long long *host_stats;   // pinned
+    int *host_count;         // pinned, 1 int
+    // the last adjoint window (fsl_window_forward)
+    void *adj_ws;
+    int adj_window, adj_ckpt, adj_cap, adj_valid;
 };
 
 namespace {
@@ -195,6 +200,113 @@ int record_graph(fsl_ctx *c, int parity) {
     return e == cudaSuccess ? FSL_OK : FSL_ECUDA;
 }
 
+// ---- adjoint workspace -------------------------------------------------------------
+// Every array is 256-byte aligned.  Checkpoint s holds (f', m, phi) of step
+// s*K; in-segment slot t (1..K) the same of step t of a recomputed segment,
+// and curvature/normal slot t (0..K-1) the values step t used.
+constexpr int ADJ_MAX_PARTIALS = 4096;
+
+struct AdjLayout {
+    size_t wcounts, wlist, widx, wseg, ckpt, slot, kn, fb0, fb1, gb, mb, pb, kb, jac, jval, dlist, part, acc, total;
+    size_t state_bytes;  // one (f', m, phi) record
+    size_t kn_bytes;     // one (kappa, normal) record
+    int nseg_ckpt;
+};
+
+AdjLayout adj_layout(const fsl_params &p, int W, int K, int cap) {
+    const size_t N = (size_t)p.nx * p.ny * p.nz;
+    AdjLayout A;
+    A.state_bytes = up(19 * N * sizeof(float)) + 2 * up(N * sizeof(float));
+    A.kn_bytes = up(N * sizeof(float)) + up(N * sizeof(float4));
+    A.nseg_ckpt = (W + K - 1) / K;
+    size_t o = 0;
+    A.wcounts = o; o += up(C_NCOUNT * sizeof(int));
+    A.wlist = o; o += up(N * sizeof(int));
+    A.widx = o; o += up(N * sizeof(int));
+    A.wseg = o; o += up(nseg_of(p) * sizeof(int));
+    A.ckpt = o; o += (size_t)A.nseg_ckpt * A.state_bytes;
+    A.slot = o; o += (size_t)K * A.state_bytes;
+    A.kn = o; o += (size_t)K * A.kn_bytes;
+    A.fb0 = o; o += up(19 * N * sizeof(float));
+    A.fb1 = o; o += up(19 * N * sizeof(float));
+    A.gb = o; o += up(19 * N * sizeof(float));
+    A.mb = o; o += up(N * sizeof(float));
+    A.pb = o; o += up(N * sizeof(float));
+    A.kb = o; o += up(N * sizeof(float));
+    A.jac = o; o += up((size_t)cap * JAC_STRIDE * sizeof(float));
+    A.jval = o; o += up((size_t)cap * sizeof(float));
+    A.dlist = o; o += up((size_t)cap * sizeof(int));
+    A.part = o; o += up(2 * ADJ_MAX_PARTIALS * sizeof(double));
+    A.acc = o; o += up(2 * sizeof(double));
+    A.total = o;
+    return A;
+}
+
+// (f', m, phi) pointers of a record at byte offset off
+struct StatePtrs {
+    float *f, *m, *phi;
+};
+StatePtrs state_at(char *ws, size_t off, size_t N) {
+    StatePtrs r;
+    r.f = reinterpret_cast<float *>(ws + off);
+    r.m = reinterpret_cast<float *>(ws + off + up(19 * N * sizeof(float)));
+    r.phi = reinterpret_cast<float *>(ws + off + up(19 * N * sizeof(float)) + up(N * sizeof(float)));
+    return r;
+}
+
+bool adjoint_supported(const fsl_params &p) {
+    return p.storage == FSL_F32 && (p.curv_model == FSL_CURV_LSQR || p.curv_model == FSL_CURV_NONE) && p.nx >= 7 &&
+           p.ny >= 7 && p.nz >= 7;
+}
+
+// Kernel view of a window: frozen types, the window's own interface list,
+// active segments and counters (the context's lists are not touched).
+Dev window_dev(const fsl_ctx *c, char *ws, const AdjLayout &A) {
+    Dev d = c->base;
+    d.flags = c->fields.flags[0];
+    d.counts = reinterpret_cast<int *>(ws + A.wcounts);
+    d.iflist = reinterpret_cast<int *>(ws + A.wlist);
+    d.iflist_next = nullptr;
+    d.cif = C_IF0;
+    d.cif_next = C_IF1;
+    d.seg_list = reinterpret_cast<int *>(ws + A.wseg);
+    d.frozen = 1;
+    return d;
+}
+
+Adj adj_args(char *ws, const AdjLayout &A, int cap) {
+    Adj a;
+    memset(&a, 0, sizeof a);
+    a.wlist = reinterpret_cast<const int *>(ws + A.wlist);
+    a.widx = reinterpret_cast<const int *>(ws + A.widx);
+    a.cap = cap;
+    a.jac = reinterpret_cast<float *>(ws + A.jac);
+    a.jval = reinterpret_cast<float *>(ws + A.jval);
+    a.dlist = reinterpret_cast<int *>(ws + A.dlist);
+    a.gb = reinterpret_cast<float *>(ws + A.gb);
+    a.mb = reinterpret_cast<float *>(ws + A.mb);
+    a.pb = reinterpret_cast<float *>(ws + A.pb);
+    a.kb = reinterpret_cast<float *>(ws + A.kb);
+    a.part = reinterpret_cast<double *>(ws + A.part);
+    a.acc = reinterpret_cast<double *>(ws + A.acc);
+    const int nb = adj_blocks();
+    a.nblk = nb < ADJ_MAX_PARTIALS ? nb : ADJ_MAX_PARTIALS;
+    return a;
+}
+
+// window setup from the context's current lists; returns the interface count
+int window_setup(fsl_ctx *c, char *ws, const AdjLayout &A, int *n_out) {
+    const Dev src = dev_for(c, c->parity);
+    int *wc = reinterpret_cast<int *>(ws + A.wcounts);
+    CK(cudaMemsetAsync(wc, 0, C_NCOUNT * sizeof(int), c->stream));
+    launch_window_setup(src, wc, reinterpret_cast<int *>(ws + A.wlist), reinterpret_cast<int *>(ws + A.widx),
+                        reinterpret_cast<int *>(ws + A.wseg), c->stream);
+    CK(cudaMemcpyAsync(c->host_count, wc + C_IF0, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *n_out = *c->host_count;
+    return FSL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -235,7 +347,8 @@ int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *ph
         if (cudaStreamCreateWithFlags(&c->cap_side, cudaStreamNonBlocking) != cudaSuccess) break;
         if (cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess) break;
         if (cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) break;
-        if (cudaMallocHost((void **)&c->host_mass, 2 * sizeof(double)) != cudaSuccess) break;
+        if (cudaMallocHost((void **)&c->host_mass, 4 * sizeof(double)) != cudaSuccess) break;
+        if (cudaMallocHost((void **)&c->host_count, sizeof(int)) != cudaSuccess) break;
         if (cudaMallocHost((void **)&c->host_stats, 16 * sizeof(long long)) != cudaSuccess) break;
         const size_t N = (size_t)c->base.N;
         cudaStream_t s = c->stream;
@@ -274,6 +387,7 @@ int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *ph
 
 int fsl_refresh(fsl_ctx *c) {
     if (!c) return FSL_EINVAL;
+    c->adj_valid = 0;
     Dev d = dev_for(c, c->parity);
     CK(cudaMemsetAsync(d.counts, 0, C_NCOUNT * sizeof(int), c->stream));
     CK(cudaMemsetAsync(d.seg_active, 0, d.nseg, c->stream));
@@ -284,6 +398,7 @@ int fsl_refresh(fsl_ctx *c) {
 
 int fsl_step(fsl_ctx *c, int nsteps) {
     if (!c || nsteps < 0) return FSL_EINVAL;
+    if (nsteps > 0) c->adj_valid = 0;
     if (c->p.curv_model == FSL_CURV_MLP && !c->base.mlp_params) return FSL_EINVAL;
     for (int s = 0; s < nsteps; ++s) {
         if (!c->graph[c->parity]) {
@@ -298,6 +413,7 @@ int fsl_step(fsl_ctx *c, int nsteps) {
 
 int fsl_step_profile(fsl_ctx *c, float ms_out[6]) {
     if (!c || !ms_out) return FSL_EINVAL;
+    c->adj_valid = 0;
     cudaEvent_t ev[7];
     for (int k = 0; k < 7; ++k)
         if (cudaEventCreate(&ev[k]) != cudaSuccess) return FSL_ECUDA;
@@ -379,6 +495,167 @@ int fsl_stats(fsl_ctx *c, int64_t counts_out[10]) {
     return FSL_OK;
 }
 
+size_t fsl_adjoint_workspace_size(const fsl_params *params, int window, int ckpt_every, int max_interface) {
+    if (!valid_params(params) || window < 1 || ckpt_every < 1 || max_interface < 1) return 0;
+    const int K = ckpt_every < window ? ckpt_every : window;
+    return adj_layout(*params, window, K, max_interface).total;
+}
+
+int fsl_set_surface(fsl_ctx *c, double sigma, double theta) {
+    if (!c || !isfinite(sigma) || !isfinite(theta)) return FSL_EINVAL;
+    c->p.sigma = sigma;
+    c->p.theta = theta;
+    c->base.six_sigma = (float)(6.0 * sigma);
+    c->base.cos_theta = (float)cos(theta);
+    c->base.sin_theta = (float)sin(theta);
+    c->base.cos_theta_d = cos(theta);
+    c->base.sin_theta_d = sin(theta);
+    for (int k = 0; k < 2; ++k)
+        if (c->graph[k]) {
+            cudaGraphExecDestroy(c->graph[k]);
+            c->graph[k] = nullptr;
+        }
+    c->adj_valid = 0;
+    return FSL_OK;
+}
+
+int fsl_window_forward(fsl_ctx *c, int window, int ckpt_every, int max_interface, void *adj_ws, size_t adj_bytes) {
+    if (!c || window < 1 || ckpt_every < 1 || max_interface < 1 || !aligned(adj_ws)) return FSL_EINVAL;
+    if (!adjoint_supported(c->p)) return FSL_EUNSUPPORTED;
+    const int K = ckpt_every < window ? ckpt_every : window;
+    const AdjLayout A = adj_layout(c->p, window, K, max_interface);
+    if (adj_bytes < A.total) return FSL_EINVAL;
+    c->adj_valid = 0;
+    char *ws = static_cast<char *>(adj_ws);
+    const size_t N = (size_t)c->base.N;
+    int nif = 0;
+    const int rc = window_setup(c, ws, A, &nif);
+    if (rc != FSL_OK) return rc;
+    if (nif > max_interface) return FSL_ECAPACITY;
+    Dev d = window_dev(c, ws, A);
+    int par = c->parity;
+    for (int t = 0; t < window; ++t) {
+        if (t % K == 0) {
+            const StatePtrs ck = state_at(ws, A.ckpt + (size_t)(t / K) * A.state_bytes, N);
+            CK(cudaMemcpyAsync(ck.f, c->fields.f[par], 19 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+            CK(cudaMemcpyAsync(ck.m, c->fields.mass, N * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+            CK(cudaMemcpyAsync(ck.phi, c->fields.phi, N * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+        }
+        d.fsrc = c->fields.f[par];
+        d.fdst = c->fields.f[par ^ 1];
+        d.mass = c->fields.mass;
+        d.phi = c->fields.phi;
+        d.kappa = c->fields.kappa;
+        d.normal = c->base.normal;
+        launch_frozen_step(d, c->stream);
+        par ^= 1;
+    }
+    launch_window_finish(dev_for(c, par), reinterpret_cast<int *>(ws + A.wcounts),
+                         reinterpret_cast<int *>(ws + A.wlist), c->stream);
+    if (cudaGetLastError() != cudaSuccess) return FSL_ECUDA;
+    c->parity = par;
+    c->adj_ws = adj_ws;
+    c->adj_window = window;
+    c->adj_ckpt = K;
+    c->adj_cap = max_interface;
+    c->adj_valid = 1;
+    return FSL_OK;
+}
+
+int fsl_window_adjoint(fsl_ctx *c, const float *dL_dphi, double *dL_dsigma, double *dL_dtheta, float *dL_dphi0,
+                       float *dL_dmass0, float *dL_df0) {
+    if (!c || !dL_dphi || !c->adj_valid) return FSL_EINVAL;
+    const int W = c->adj_window, K = c->adj_ckpt;
+    const AdjLayout A = adj_layout(c->p, W, K, c->adj_cap);
+    char *ws = static_cast<char *>(c->adj_ws);
+    const size_t N = (size_t)c->base.N;
+    cudaStream_t st = c->stream;
+    Adj a = adj_args(ws, A, c->adj_cap);
+    float *fb[2] = {reinterpret_cast<float *>(ws + A.fb0), reinterpret_cast<float *>(ws + A.fb1)};
+    CK(cudaMemsetAsync(fb[0], 0, 19 * N * sizeof(float), st));
+    CK(cudaMemsetAsync(fb[1], 0, 19 * N * sizeof(float), st));
+    CK(cudaMemsetAsync(a.mb, 0, N * sizeof(float), st));
+    CK(cudaMemsetAsync(a.pb, 0, N * sizeof(float), st));
+    CK(cudaMemsetAsync(a.kb, 0, N * sizeof(float), st));
+    CK(cudaMemsetAsync(a.acc, 0, 2 * sizeof(double), st));
+    Dev w = window_dev(c, ws, A);
+    launch_adjoint_seed(w, a, dL_dphi, st);
+    int cur = 0;  // fb[cur] holds the adjoint of f' at the step after the one being reversed
+    for (int sgm = A.nseg_ckpt - 1; sgm >= 0; --sgm) {
+        const int len = (W - sgm * K) < K ? (W - sgm * K) : K;
+        const StatePtrs ck = state_at(ws, A.ckpt + (size_t)sgm * A.state_bytes, N);
+        auto state = [&](int t) { return t == 0 ? ck : state_at(ws, A.slot + (size_t)(t - 1) * A.state_bytes, N); };
+        auto kn = [&](int t, float **kap, float4 **nrm) {
+            char *b = ws + A.kn + (size_t)t * A.kn_bytes;
+            *kap = reinterpret_cast<float *>(b);
+            *nrm = reinterpret_cast<float4 *>(b + up(N * sizeof(float)));
+        };
+        // recompute the segment, keeping every state
+        for (int t = 0; t < len; ++t) {
+            const StatePtrs s0 = state(t), s1 = state(t + 1);
+            CK(cudaMemcpyAsync(s1.m, s0.m, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(s1.phi, s0.phi, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            Dev d = w;
+            d.fsrc = s0.f;
+            d.fdst = s1.f;
+            d.mass = s1.m;
+            d.phi = s1.phi;
+            kn(t, &d.kappa, &d.normal);
+            launch_frozen_step(d, st);
+        }
+        // reverse it
+        for (int t = len - 1; t >= 0; --t) {
+            const StatePtrs s0 = state(t);
+            Dev d = w;
+            d.fsrc = s0.f;
+            d.fdst = nullptr;
+            d.mass = s0.m;
+            d.phi = s0.phi;
+            kn(t, &d.kappa, &d.normal);
+            a.fb_in = fb[cur];
+            a.fb_out = fb[cur ^ 1];
+            launch_adjoint_step(d, a, st);
+            cur ^= 1;
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess) return FSL_ECUDA;
+    if (dL_dphi0) CK(cudaMemcpyAsync(dL_dphi0, a.pb, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (dL_dmass0) CK(cudaMemcpyAsync(dL_dmass0, a.mb, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (dL_df0) CK(cudaMemcpyAsync(dL_df0, fb[cur], 19 * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(c->host_mass + 2, a.acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (dL_dsigma) *dL_dsigma = c->host_mass[2];
+    if (dL_dtheta) *dL_dtheta = c->host_mass[3];
+    int status = 0;
+    CK(cudaMemcpy(&status, c->base.status, sizeof(int), cudaMemcpyDeviceToHost));
+    return status ? status : FSL_OK;
+}
+
+int fsl_kappa_jacobian(fsl_ctx *c, void *adj_ws, size_t adj_bytes, int max_interface, float *jac_out,
+                       int32_t *cells_out, float *kappa_out, int *n_out) {
+    if (!c || max_interface < 1 || !aligned(adj_ws) || !jac_out || !cells_out || !kappa_out || !n_out)
+        return FSL_EINVAL;
+    if (!adjoint_supported(c->p)) return FSL_EUNSUPPORTED;
+    const AdjLayout A = adj_layout(c->p, 1, 1, max_interface);
+    if (adj_bytes < A.total) return FSL_EINVAL;
+    char *ws = static_cast<char *>(adj_ws);
+    if (adj_ws == c->adj_ws) c->adj_valid = 0;  // the window's buffers are reused
+    int nif = 0;
+    const int rc = window_setup(c, ws, A, &nif);
+    if (rc != FSL_OK) return rc;
+    *n_out = nif;
+    if (nif > max_interface) return FSL_ECAPACITY;
+    Adj a = adj_args(ws, A, max_interface);
+    a.jac = jac_out;
+    a.jval = kappa_out;
+    Dev d = window_dev(c, ws, A);
+    d.phi = c->fields.phi;
+    launch_kappa_jacobian(d, a, c->stream);
+    CK(cudaMemcpyAsync(cells_out, a.wlist, (size_t)nif * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
+}
+
 int fsl_parity(const fsl_ctx *c) { return c ? c->parity : FSL_EINVAL; }
 
 int fsl_status(fsl_ctx *c) {
@@ -412,6 +689,7 @@ void fsl_destroy(fsl_ctx *c) {
     if (c->join) cudaEventDestroy(c->join);
     if (c->host_mass) cudaFreeHost(c->host_mass);
     if (c->host_stats) cudaFreeHost(c->host_stats);
+    if (c->host_count) cudaFreeHost(c->host_count);
     delete c;
 }
 

@@ -48,7 +48,7 @@ enum : uint8_t {
 // device counters in the workspace: interface-list lengths of the two list
 // buffers, conversion lists, FP64 LSQR re-solves, active segments
 enum { C_IF0 = 0, C_IF1 = 1, C_FILL = 2, C_EMPTY = 3, C_NEWGAS = 4, C_LIQ2IF = 5, C_FP64 = 6, C_SEG = 7, C_SLOW = 8,
-       C_MLP = 9, C_MLPKEEP = 10, C_NCOUNT = 16 };
+       C_MLP = 9, C_MLPKEEP = 10, C_ADJ64 = 11, C_NCOUNT = 16 };
 
 // the grid is walked in x-row segments of SEG cells (one warp each); a
 // segment is active while it holds a liquid or interface cell
@@ -81,6 +81,7 @@ struct Dev {
     long long *stats;
     // method parameters
     int collision, storage, plic_iters, curv_model;
+    int frozen;              // 1: cell types frozen (no conversion test; adjoint windows)
     float omega_e, omega_o;  // 1/tau_even, 1/tau_odd
     float rho_gas, six_sigma, eps;
     float cos_theta, sin_theta;
@@ -235,6 +236,7 @@ void launch_lsqr(const Dev &d, float *kappa_out, cudaStream_t s);
 void launch_fd(const Dev &d, float *kappa_out, cudaStream_t s);
 void launch_zero_kappa(const Dev &d, float *kappa_out, cudaStream_t s);
 void launch_mlp_curv(const Dev &d, float *kappa_out, cudaStream_t s);
+void launch_fin_frozen(const Dev &d, cudaStream_t s);
 
 int max_partials();
 // blocks of `block` threads of `kernel` that are resident on the whole GPU at once

@@ -1,0 +1,610 @@
+// k_adj.cu -- reverse (adjoint) pass of the FSLBM step over a window of time
+// steps with frozen cell types, and the curvature Jacobian it needs.
+//
+// With the types frozen the step is a smooth map of the state (post-collision
+// PDFs f, interface mass m, fill level phi = m / rho) and of the parameters
+// sigma and theta:
+//   kappa  = K(phi; theta)                         LSQR fit, Sec. II.C
+//   g_q(x) = f_q(x - c_q)                          fluid source (Eq. lbe1)
+//          = f_qbar(x)                             obstacle (bounce-back)
+//          = 2 w_q rho_b (1 + 9/2 (c_q.u)^2 - 3/2 u^2) - f_qbar(x)
+//                                                  gas source (Eq. reconstruct),
+//            rho_b = 3 p_g + 6 sigma kappa(x), u = u(x, t)
+//   f(t+1) = C(g)                                  BGK / TRT collision (Eq. lbe2)
+//   m(t+1) = m + sum_q k_q (f_q(x - c_q) - f_qbar(x)),  k_q = 1 from a liquid
+//            source, (phi(x) + phi(x - c_q)) / 2 from an interface source
+//            (Eqs. advection1/2)
+//   phi(t+1) = m(t+1) / rho(t+1),  rho(t+1) = sum_q g_q
+// The reverse of one step, given the adjoints (F, M, P) of (f, m, phi) at
+// t+1, runs as five kernels:
+//   k_adj_iface   interface cells: phi(t+1) = m / rho adjoint, collision
+//                 adjoint of g, and every dependency of x's own outputs on
+//                 x's own inputs (reconstruction, bounce-back, outflow of the
+//                 mass exchange, u_b, rho_b -> kappa and sigma)
+//   k_adj_bulk    liquid cells: collision adjoint of g
+//   k_adj_gather  every fluid cell y: the adjoint of f_r(y) gathered from the
+//                 cells that read it (y + c_r streams it; an interface cell
+//                 y + c_r also exchanges mass with it), and for interface y
+//                 the adjoint of phi(y) through the exchange weights k_q
+//   k_adj_curv    interface cells y: adjoint of phi(y) through the curvature
+//                 of the interface cells x of the 7x7x7 window around it,
+//                 sum_x kbar(x) dkappa_x/dphi_y, and dL/dtheta
+//   k_adj_accum   fixed-order sum of the per-block sigma and theta partials
+// Gathers (not scatters) keep every sum in a fixed order: the result is
+// bit-reproducible.  The curvature Jacobian rows come from forward-mode dual
+// numbers through the same per-cell code as the forward LSQR fit
+// (curv_common.cuh): one warp per interface cell, one seed (a window cell's
+// phi, or theta) per lane, the fill levels and flags of the 7x7x7 window in
+// shared memory.
+#include "adjoint.cuh"
+#include "curv_common.cuh"
+
+namespace fslk {
+
+constexpr int ADJ_BLOCK = 128;
+
+int adj_blocks() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (sms > 0 ? sms : 1) * 4;
+}
+
+// ---- window bookkeeping ---------------------------------------------------------
+__global__ void k_window_setup(Dev d, int *wcounts, int *wlist, int *widx, int *wseg) {
+    int cnt[2];
+    block_counts<2>(d.counts, {d.cif, C_SEG}, cnt);
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    if (tid == 0) {
+        wcounts[C_IF0] = cnt[0];
+        wcounts[C_SEG] = cnt[1];
+    }
+    for (int k = tid; k < cnt[0]; k += nth) {
+        const int i = d.iflist[k];
+        wlist[k] = i;
+        widx[i] = k;
+    }
+    for (int k = tid; k < cnt[1]; k += nth) wseg[k] = d.seg_list[k];
+}
+
+__global__ void k_window_finish(Dev d, const int *wcounts, const int *wlist) {
+    int cnt[1];
+    block_counts<1>(wcounts, {C_IF0}, cnt);
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    if (tid == 0) d.counts[d.cif] = cnt[0];
+    for (int k = tid; k < cnt[0]; k += nth) d.iflist[k] = wlist[k];
+}
+
+void launch_window_setup(const Dev &src, int *wcounts, int *wlist, int *widx, int *wseg, cudaStream_t s) {
+    cudaMemsetAsync(widx, 0xff, (size_t)src.N * sizeof(int), s);
+    static const int g = list_blocks((const void *)k_window_setup, 256, 2);
+    k_window_setup<<<g, 256, 0, s>>>(src, wcounts, wlist, widx, wseg);
+}
+
+void launch_window_finish(const Dev &dst, const int *wcounts, const int *wlist, cudaStream_t s) {
+    static const int g = list_blocks((const void *)k_window_finish, 256, 2);
+    k_window_finish<<<g, 256, 0, s>>>(dst, wcounts, wlist);
+}
+
+void launch_frozen_step(const Dev &d, cudaStream_t s) {
+    launch_normals(d, s);
+    if (d.curv_model == FSL_CURV_LSQR) launch_lsqr(d, d.kappa, s);
+    else launch_zero_kappa(d, d.kappa, s);
+    launch_sc_bulk(d, s);
+    launch_sc_iface(d, s);
+    launch_fin_frozen(d, s);
+}
+
+// ---- helpers --------------------------------------------------------------------
+// sum over the block in a fixed order; the result is valid in thread 0
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double ws[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) ws[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; ++w) t += ws[w];
+    __syncthreads();
+    return t;
+}
+
+// Adjoint of the collision f' = C(g) (Eq. lbe2) at g: gb = (dC/dg)^T fb.
+// C(g) = L g + w_e e+(rho, j) + w_o e-(j) with the linear part L (relaxation
+// of the even and odd parts of each pair q, qbar; symmetric) and the
+// equilibrium parts e+_q = w_q (rho + 9/2 (c_q.j)^2 / rho - 3/2 j.j / rho),
+// e-_q = 3 w_q c_q.j as functions of rho = sum g and j = sum c g.  BGK is
+// the case w_e = w_o.
+__device__ __forceinline__ void collide_adj(const float g[Q], const float fb[Q], const Dev &d, float gb[Q]) {
+    float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        rho += g[q];
+        jx += cx(q) * g[q];
+        jy += cy(q) * g[q];
+        jz += cz(q) * g[q];
+    }
+    const float inv = 1.0f / rho;
+    const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    const float u2 = ux * ux + uy * uy + uz * uz;
+    const float we = d.omega_e, wo = d.omega_o;
+    float A = 0.f, Bx = 0.f, By = 0.f, Bz = 0.f, S = 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+        const float t = fb[q] * wq(q);
+        A += t * (1.0f - 4.5f * cu * cu + 1.5f * u2);
+        const float sc = t * (9.0f * we * cu + 3.0f * wo);
+        Bx += sc * cx(q);
+        By += sc * cy(q);
+        Bz += sc * cz(q);
+        S += t;
+    }
+    A *= we;
+    // d/dj of -3/2 j.j / rho over all q: -3 w_e u sum_q fb_q w_q
+    Bx -= 3.0f * we * ux * S;
+    By -= 3.0f * we * uy * S;
+    Bz -= 3.0f * we * uz * S;
+    gb[0] = (1.0f - we) * fb[0] + A;
+#pragma unroll
+    for (int q = 1; q < Q; q += 2) {
+        const int qb = q + 1;
+        const float sp = 0.5f * (fb[q] + fb[qb]), sm = 0.5f * (fb[q] - fb[qb]);
+        const float bc = Bx * cx(q) + By * cy(q) + Bz * cz(q);
+        gb[q] = fb[q] - we * sp - wo * sm + A + bc;
+        gb[qb] = fb[qb] - we * sp + wo * sm + A - bc;
+    }
+}
+
+// ---- curvature Jacobian ---------------------------------------------------------
+// Accessor of curv_common.cuh over the 7x7x7 window of fill levels and flags
+// held in shared memory, with one seeded direction: the fill level of window
+// slot `seed`, or theta (seed == JAC_CELLS).  Normals and PLIC offsets of the
+// neighbours are recomputed in Dual<float> (as k_normals computes them in
+// float) and handed to the fit in its scalar type T.
+__device__ __forceinline__ int jac_slot(int dx, int dy, int dz) { return (dz + 3) * 49 + (dy + 3) * 7 + (dx + 3); }
+
+struct WinAcc {
+    const float *phi;
+    const uint8_t *fl;
+    int seed;
+    double ct, st;
+    int iters;
+
+    __device__ __forceinline__ uint8_t flag(int dx, int dy, int dz) const { return fl[jac_slot(dx, dy, dz)]; }
+    __device__ __forceinline__ Dual<float> phi_d(int dx, int dy, int dz) const {
+        const int s = jac_slot(dx, dy, dz);
+        return Dual<float>(phi[s], s == seed ? 1.0f : 0.0f, 0);
+    }
+    __device__ __forceinline__ Dual<float> phi_ext(int dx, int dy, int dz) const {
+        if (!(flag(dx, dy, dz) & T_OBS)) return phi_d(dx, dy, dz);
+        return reflect_value<Dual<float>>([&](int a, int b, int c) { return flag(dx + a, dy + b, dz + c); },
+                                          [&](int a, int b, int c) { return phi_d(dx + a, dy + b, dz + c); });
+    }
+    template <typename T>
+    __device__ __forceinline__ bool normal(int dx, int dy, int dz, T n[3], T &a) const {
+        using DF = Dual<float>;
+        DF nv[3], af;
+        if (flag(dx, dy, dz) & B_NEAR)
+            parker_youngs<DF>([&](int ex, int ey, int ez) { return phi_ext(dx + ex, dy + ey, dz + ez); }, nv);
+        else
+            parker_youngs<DF>([&](int ex, int ey, int ez) { return phi_d(dx + ex, dy + ey, dz + ez); }, nv);
+        if (!unit_normal_offset<DF>(nv, phi_d(dx, dy, dz), iters, af)) return false;
+        using S = typename scalar_of<T>::type;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) n[k] = T((S)nv[k].v, (S)nv[k].d, 0);
+        a = T((S)af.v, (S)af.d, 0);
+        return true;
+    }
+    template <typename T>
+    __device__ __forceinline__ void theta(T &c, T &s) const {
+        using S = typename scalar_of<T>::type;
+        const bool sd = seed == JAC_CELLS;
+        c = T((S)ct, sd ? (S)(-st) : S(0), 0);
+        s = T((S)st, sd ? (S)ct : S(0), 0);
+    }
+};
+
+// One warp per interface cell of the window (FROM_LIST: the positions in
+// a.dlist, redone in Dual<double>).  The seeds are the interface cells of
+// the window (the only cells whose fill level varies with frozen types) and
+// theta; each lane evaluates kappa of the centre cell with its own seed and
+// stores the derivative in the cell's Jacobian row.  A cell whose FP32 fit is
+// ill conditioned (cond^2 above fp64_cond, as k_lsqr_slow decides) is listed
+// for the FP64 pass.
+constexpr int JAC_WARPS = 4;
+
+template <typename T, bool FROM_LIST>
+__global__ void __launch_bounds__(JAC_WARPS * 32) k_kappa_jac(Dev d, Adj a) {
+    __shared__ float sphi[JAC_WARPS][JAC_CELLS];
+    __shared__ uint8_t sfl[JAC_WARPS][JAC_CELLS + 1];
+    __shared__ short sseed[JAC_WARPS][JAC_STRIDE];
+    int cnt[1];
+    block_counts<1>(d.counts, {FROM_LIST ? C_ADJ64 : C_IF0}, cnt);
+    const int n = FROM_LIST ? cnt[0] : min(cnt[0], a.cap);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    float *wphi = sphi[w];
+    uint8_t *wfl = sfl[w];
+    short *wseed = sseed[w];
+    for (int t = gw; t < n; t += nwarps) {
+        const int k = FROM_LIST ? a.dlist[t] : t;
+        const int i = a.wlist[k];
+        int x, y, z;
+        cell_coords(d, i, x, y, z);
+        for (int sl = lane; sl < JAC_CELLS; sl += 32) {
+            const int j = nbr_index(d, x, y, z, sl % 7 - 3, (sl / 7) % 7 - 3, sl / 49 - 3);
+            wphi[sl] = d.phi[j];
+            wfl[sl] = d.flags[j];
+        }
+        __syncwarp();
+        int ns = 0;
+        for (int base = 0; base < JAC_CELLS; base += 32) {
+            const int sl = base + lane;
+            const bool p = sl < JAC_CELLS && (wfl[sl] & T_IF);
+            const unsigned m = __ballot_sync(0xffffffffu, p);
+            if (p) wseed[ns + __popc(m & ((1u << lane) - 1u))] = (short)sl;
+            ns += __popc(m);
+        }
+        if (lane == 0) wseed[ns] = (short)JAC_CELLS;
+        ++ns;
+        __syncwarp();
+        bool redo = false;
+        for (int base = 0; base < ns; base += 32) {
+            const int idx = base + lane;
+            const WinAcc acc{wphi, wfl, idx < ns ? (int)wseed[idx] : -1, d.cos_theta_d, d.sin_theta_d, d.plic_iters};
+            T cond;
+            const T kap = lsqr_core<T>(acc, wfl[JAC_CENTRE], cond);
+            if (!FROM_LIST && (float)(cond.v * cond.v) > d.fp64_cond) {
+                redo = true;  // same value on every lane
+                break;
+            }
+            if (idx < ns) a.jac[(size_t)k * JAC_STRIDE + wseed[idx]] = (float)kap.d;
+            if (base == 0 && lane == 0) a.jval[k] = (float)kap.v;
+        }
+        if (redo && lane == 0) a.dlist[atomicAdd(d.counts + C_ADJ64, 1)] = k;
+        __syncwarp();
+    }
+    if (!FROM_LIST && blockIdx.x == 0 && threadIdx.x == 0 && cnt[0] > a.cap) set_status(d.status, FSL_ECAPACITY);
+}
+
+void launch_kappa_jacobian(const Dev &d, const Adj &a, cudaStream_t s) {
+    static const int g = list_blocks((const void *)k_kappa_jac<Dual<float>, false>, JAC_WARPS * 32, 4);
+    static const int g64 = list_blocks((const void *)k_kappa_jac<Dual<double>, true>, JAC_WARPS * 32, 1);
+    cudaMemsetAsync(d.counts + C_ADJ64, 0, sizeof(int), s);
+    k_kappa_jac<Dual<float>, false><<<g, JAC_WARPS * 32, 0, s>>>(d, a);
+    k_kappa_jac<Dual<double>, true><<<g64, JAC_WARPS * 32, 0, s>>>(d, a);
+}
+
+// ---- reverse of the stream-collide, boundary condition and mass exchange ---------
+// source of direction q of cell (x, y, z): x - c_q (periodic)
+__device__ __forceinline__ void adj_sources(const Dev &d, int x, int y, int z, int src[Q]) {
+    const int xs[3] = {x == d.nx - 1 ? 0 : x + 1, x, x == 0 ? d.nx - 1 : x - 1};
+    const int ys[3] = {y == d.ny - 1 ? 0 : y + 1, y, y == 0 ? d.ny - 1 : y - 1};
+    const int zs[3] = {z == d.nz - 1 ? 0 : z + 1, z, z == 0 ? d.nz - 1 : z - 1};
+#pragma unroll
+    for (int q = 0; q < Q; ++q) src[q] = cell_index(d, xs[cx(q) + 1], ys[cy(q) + 1], zs[cz(q) + 1]);
+}
+
+// Interface cells (window list), one thread per cell; recomputes the
+// forward step of the cell (as k_sc_iface) and reverses it.  Writes the
+// adjoint of the pre-collision PDFs (gb), the cell's own contribution to the
+// adjoint of its post-collision PDFs at t (fb_out), the adjoint of m(t+1)
+// after the phi = m / rho link (mb, in place: it is also the adjoint of m(t)
+// before phi(t) is accounted for), kbar (kb) and the block's sigma partial.
+__global__ void __launch_bounds__(ADJ_BLOCK) k_adj_iface(Dev d, Adj a) {
+    int cnt[1];
+    block_counts<1>(d.counts, {C_IF0}, cnt);
+    const int n = cnt[0];
+    const long long N = d.N;
+    const float *fs = static_cast<const float *>(d.fsrc);
+    double sig = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int i = a.wlist[k];
+        int x, y, z;
+        cell_coords(d, i, x, y, z);
+        int src[Q];
+        adj_sources(d, x, y, z, src);
+        float fo[Q], g[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) fo[q] = __ldg(fs + (long long)q * N + i);
+        uint8_t tq[Q];
+        bool has_gas = false, has_obs = false;
+        float wx = 0.f, wy = 0.f, wz = 0.f;
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            tq[q] = d.flags[src[q]] & T_MASK;
+            has_gas |= (tq[q] & T_GAS) != 0;
+            if (tq[q] & T_OBS) {
+                has_obs = true;
+                wx -= cx(q);
+                wy -= cy(q);
+                wz -= cz(q);
+            }
+        }
+        float r0 = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            r0 += fo[q];
+            jx += cx(q) * fo[q];
+            jy += cy(q) * fo[q];
+            jz += cz(q) * fo[q];
+        }
+        const float ux = jx / r0, uy = jy / r0, uz = jz / r0;
+        const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+        const float kap = d.kappa[i];
+        const float rho_b = d.rho_gas + d.six_sigma * kap;
+        const bool corner = has_gas && has_obs;
+        float ntx = 0.f, nty = 0.f, ntz = 0.f;
+        if (corner) {
+            const float4 n4 = d.normal[i];
+            const float wl = rsqrtf(wx * wx + wy * wy + wz * wz);
+            wx *= wl;
+            wy *= wl;
+            wz *= wl;
+            const float wn = n4.x * wx + n4.y * wy + n4.z * wz;
+            ntx = n4.x - wn * wx;
+            nty = n4.y - wn * wy;
+            ntz = n4.z - wn * wz;
+        }
+        const float phix = d.phi[i];
+        // forward: g, the link kinds, the exchange weights, dm
+        unsigned fluid = 0u, recon = 0u;
+        float kw[Q];
+        float dm = 0.f;
+        g[0] = fo[0];
+        kw[0] = 0.f;
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            const int qb = opp(q);
+            const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+            const float rc = 2.0f * wq(q) * rho_b * (1.0f + 4.5f * cu * cu - uu) - fo[qb];
+            kw[q] = 0.f;
+            if (tq[q] & (T_LIQ | T_IF)) {
+                const float fin = __ldg(fs + (long long)q * N + src[q]);
+                g[q] = fin;
+                kw[q] = (tq[q] & T_LIQ) ? 1.0f : 0.5f * (phix + d.phi[src[q]]);
+                dm += kw[q] * (fin - fo[qb]);
+                fluid |= 1u << q;
+            } else if (tq[q] & T_OBS) {
+                const float outdir = -(cx(q) * ntx + cy(q) * nty + cz(q) * ntz);
+                if (corner && outdir < 0.f) {
+                    g[q] = rc;
+                    recon |= 1u << q;
+                } else {
+                    g[q] = fo[qb];
+                }
+            } else {
+                g[q] = rc;
+                recon |= 1u << q;
+            }
+        }
+        float rho1 = 0.f;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) rho1 += g[q];
+        const float m1 = d.mass[i] + dm;
+        // reverse: phi(t+1) = m(t+1) / rho(t+1)
+        float fb[Q], gb[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) fb[q] = a.fb_in[(long long)q * N + i];
+        const float pb1 = a.pb[i];
+        const float mbar = a.mb[i] + pb1 / rho1;
+        const float rhobar = -pb1 * m1 / (rho1 * rho1);
+        collide_adj(g, fb, d, gb);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            gb[q] += rhobar;
+            a.gb[(long long)q * N + i] = gb[q];
+        }
+        // reverse of the links: own PDFs at t, rho_b, u_b
+        float own[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) own[q] = 0.f;
+        own[0] = gb[0];
+        float rbb = 0.f, ubx = 0.f, uby = 0.f, ubz = 0.f;
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            const int qb = opp(q);
+            if (fluid & (1u << q)) {
+                own[qb] -= kw[q] * mbar;
+            } else if (recon & (1u << q)) {
+                const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+                own[qb] -= gb[q];
+                rbb += gb[q] * 2.0f * wq(q) * (1.0f + 4.5f * cu * cu - uu);
+                const float s = gb[q] * 2.0f * wq(q) * rho_b;
+                ubx += s * (9.0f * cu * cx(q) - 3.0f * ux);
+                uby += s * (9.0f * cu * cy(q) - 3.0f * uy);
+                ubz += s * (9.0f * cu * cz(q) - 3.0f * uz);
+            } else {
+                own[qb] += gb[q];
+            }
+        }
+        // u = j / r0 of the own PDFs: du/dfo_r = (c_r - u) / r0
+        const float ir0 = 1.0f / r0;
+#pragma unroll
+        for (int r = 0; r < Q; ++r)
+            own[r] += ((cx(r) - ux) * ubx + (cy(r) - uy) * uby + (cz(r) - uz) * ubz) * ir0;
+#pragma unroll
+        for (int r = 0; r < Q; ++r) a.fb_out[(long long)r * N + i] = own[r];
+        a.mb[i] = mbar;
+        a.kb[i] = d.six_sigma * rbb;
+        sig += 6.0 * (double)kap * (double)rbb;
+    }
+    const double t = block_sum(sig);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = t;
+}
+
+// Liquid cells of the active segments: recomputed pull (bounce-back at wall
+// links) and the collision adjoint.
+__global__ void __launch_bounds__(256) k_adj_bulk(Dev d, Adj a) {
+    int cnt[1];
+    block_counts<1>(d.counts, {C_SEG}, cnt);
+    const int nseg = cnt[0];
+    const long long N = d.N;
+    const float *fs = static_cast<const float *>(d.fsrc);
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int k = gw; k < nseg; k += nw) {
+        const int s = d.seg_list[k];
+        const int row = s / d.nsegx;
+        const int x = (s - row * d.nsegx) * SEG + lane;
+        const int z = row / d.ny, y = row - z * d.ny;
+        if (x >= d.nx) continue;
+        const int i = cell_index(d, x, y, z);
+        const uint8_t fl = d.flags[i];
+        if (!(fl & T_LIQ)) continue;
+        int src[Q];
+        adj_sources(d, x, y, z, src);
+        float g[Q], fb[Q], gb[Q];
+        g[0] = __ldg(fs + i);
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            const bool wall = (fl & B_NEAR) && (d.flags[src[q]] & T_OBS);
+            g[q] = wall ? __ldg(fs + (long long)opp(q) * N + i) : __ldg(fs + (long long)q * N + src[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) fb[q] = a.fb_in[(long long)q * N + i];
+        collide_adj(g, fb, d, gb);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) a.gb[(long long)q * N + i] = gb[q];
+    }
+}
+
+// Every fluid cell y of the active segments: the adjoint of f_r(y, t) is
+// gathered from its readers.  The cell y + c_r (fluid) pulls it as its g_r;
+// an interface cell y + c_r also takes k_r (f_r(y) - ...) into its mass; a
+// liquid y at an obstacle link takes it back as g_rbar(y).  Interface y add
+// their own part (k_adj_iface) and get the exchange-weight part of the
+// adjoint of phi(y): 1/2 sum over interface sources y - c_p of
+// (mbar(y) - mbar(y - c_p)) (f_p(y - c_p) - f_pbar(y)).
+__global__ void __launch_bounds__(256) k_adj_gather(Dev d, Adj a) {
+    int cnt[1];
+    block_counts<1>(d.counts, {C_SEG}, cnt);
+    const int nseg = cnt[0];
+    const long long N = d.N;
+    const float *fs = static_cast<const float *>(d.fsrc);
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int k = gw; k < nseg; k += nw) {
+        const int s = d.seg_list[k];
+        const int row = s / d.nsegx;
+        const int x = (s - row * d.nsegx) * SEG + lane;
+        const int z = row / d.ny, y = row - z * d.ny;
+        if (x >= d.nx) continue;
+        const int i = cell_index(d, x, y, z);
+        const uint8_t fl = d.flags[i];
+        if (!(fl & (T_LIQ | T_IF))) continue;
+        const bool isif = (fl & T_IF) != 0;
+        int src[Q];
+        adj_sources(d, x, y, z, src);  // src[opp(r)] = y + c_r
+        const float phiy = isif ? d.phi[i] : 1.0f;
+        const float mby = isif ? a.mb[i] : 0.f;
+        float pbar = 0.f;
+        {
+            const float v = isif ? 0.f : a.gb[i];
+            a.fb_out[i] = isif ? a.fb_out[i] + v : v;
+        }
+#pragma unroll
+        for (int r = 1; r < Q; ++r) {
+            const int rb = opp(r);
+            const int xn = src[rb];
+            const uint8_t tx = d.flags[xn];
+            float v = 0.f;
+            if (tx & (T_LIQ | T_IF)) {
+                v = a.gb[(long long)r * N + xn];
+                if (tx & T_IF) v += (isif ? 0.5f * (d.phi[xn] + phiy) : 1.0f) * a.mb[xn];
+            } else if ((tx & T_OBS) && !isif) {
+                v = a.gb[(long long)rb * N + i];
+            }
+            const long long o = (long long)r * N + i;
+            a.fb_out[o] = isif ? a.fb_out[o] + v : v;
+            // exchange weight of the link from the source y - c_r (direction r)
+            if (isif && (d.flags[src[r]] & T_IF)) {
+                const int sr = src[r];
+                pbar += (mby - a.mb[sr]) * (__ldg(fs + (long long)r * N + sr) - __ldg(fs + (long long)rb * N + i));
+            }
+        }
+        if (isif) a.pb[i] = 0.5f * pbar;
+    }
+}
+
+// Interface cells y (window list), one warp each: the curvature part of the
+// adjoint of phi(y), sum over the interface cells x of the 7x7x7 window of
+// kbar(x) dkappa_x/dphi_y (row of x, slot of y - x), and the block's theta
+// partial kbar(y) dkappa_y/dtheta.
+__global__ void __launch_bounds__(ADJ_BLOCK) k_adj_curv(Dev d, Adj a) {
+    int cnt[1];
+    block_counts<1>(d.counts, {C_IF0}, cnt);
+    const int n = cnt[0];
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    double th = 0.0;
+    for (int k = gw; k < n; k += nwarps) {
+        const int i = a.wlist[k];
+        int x, y, z;
+        cell_coords(d, i, x, y, z);
+        float acc = 0.f;
+        for (int sl = lane; sl < JAC_CELLS; sl += 32) {
+            const int j = nbr_index(d, x, y, z, sl % 7 - 3, (sl / 7) % 7 - 3, sl / 49 - 3);
+            if (!(d.flags[j] & T_IF)) continue;
+            const int kx = a.widx[j];
+            if (kx < 0 || kx >= a.cap) continue;
+            acc += a.kb[j] * a.jac[(size_t)kx * JAC_STRIDE + (JAC_CELLS - 1 - sl)];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            a.pb[i] += acc;
+            if (k < a.cap) th += (double)a.kb[i] * (double)a.jac[(size_t)k * JAC_STRIDE + JAC_CELLS];
+        }
+    }
+    const double t = block_sum(th);
+    if (threadIdx.x == 0) a.part[a.nblk + blockIdx.x] = t;
+}
+
+// acc[0] += sum of the sigma partials, acc[1] += sum of the theta partials
+// (fixed order)
+__global__ void __launch_bounds__(256) k_adj_accum(Adj a, int with_theta) {
+    double s = 0.0, t = 0.0;
+    for (int b = threadIdx.x; b < a.nblk; b += blockDim.x) {
+        s += a.part[b];
+        if (with_theta) t += a.part[a.nblk + b];
+    }
+    s = block_sum(s);
+    t = block_sum(t);
+    if (threadIdx.x == 0) {
+        a.acc[0] += s;
+        a.acc[1] += t;
+    }
+}
+
+// adjoint of phi at the window's end: the interface entries of dL/dphi
+__global__ void k_adjoint_seed(Dev d, Adj a, const float *dphi) {
+    int cnt[1];
+    block_counts<1>(d.counts, {C_IF0}, cnt);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt[0]; k += gridDim.x * blockDim.x) {
+        const int i = a.wlist[k];
+        a.pb[i] = dphi[i];
+    }
+}
+
+void launch_adjoint_seed(const Dev &d, const Adj &a, const float *dL_dphi, cudaStream_t s) {
+    static const int g = list_blocks((const void *)k_adjoint_seed, 256, 2);
+    k_adjoint_seed<<<g, 256, 0, s>>>(d, a, dL_dphi);
+}
+
+void launch_adjoint_step(const Dev &d, const Adj &a, cudaStream_t s) {
+    const bool lsqr = d.curv_model == FSL_CURV_LSQR;
+    if (lsqr) launch_kappa_jacobian(d, a, s);
+    static const int gb = resident_grid((const void *)k_adj_bulk, 256);
+    static const int gg = resident_grid((const void *)k_adj_gather, 256);
+    k_adj_iface<<<a.nblk, ADJ_BLOCK, 0, s>>>(d, a);
+    k_adj_bulk<<<gb, 256, 0, s>>>(d, a);
+    k_adj_gather<<<gg, 256, 0, s>>>(d, a);
+    if (lsqr) k_adj_curv<<<a.nblk, ADJ_BLOCK, 0, s>>>(d, a);
+    k_adj_accum<<<1, 256, 0, s>>>(a, lsqr ? 1 : 0);
+}
+
+}  // namespace fslk

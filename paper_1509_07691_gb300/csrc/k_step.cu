@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(256) k_sc_bulk(Dev d) {
 //   obstacle  f_q(x) = f'_qbar(x) (bounce-back), or Eq. reconstruct at a
 //             contact-line cell when c_qbar . n_t < 0, n_t the interface normal
 //             projected into the wall (Fig. inhomo)
-// plus the mass exchange of Eqs. (advection1/2) and the conversion test.
+// plus the mass exchange of Eqs. (advection1/2) and the conversion test
+// (skipped when the types are frozen).
 template <int S, int COLL>
 __global__ void __launch_bounds__(LIST_BLOCK) k_sc_iface(Dev d) {
     using St = Store<S>;
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_sc_iface(Dev d) {
         const float m = d.mass[i] + dm;
         d.mass[i] = m;
         d.rho[i] = rho;
+        if (d.frozen) continue;
         if (m > (1.0f + d.eps) * rho) {
             d.flags[i] = fl | B_TOLIQ;
             d.fill[atomicAdd(d.counts + C_FILL, 1)] = i;
@@ -416,6 +418,23 @@ __global__ void __launch_bounds__(256) k_fin_b(Dev d) {
         const int s = base + threadIdx.x;
         block_append(d.seg_list, d.counts + C_SEG, s < d.nseg && d.seg_active[s], s);
     }
+}
+
+// Final update of a step with frozen types (no conversion, the interface
+// list and the active segments stay): phi = m / rho of the interface cells.
+__global__ void __launch_bounds__(LIST_BLOCK) k_fin_frozen(Dev d) {
+    int cnt[1];
+    block_counts<1>(d.counts, {d.cif}, cnt);
+    const int n = cnt[0];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int i = d.iflist[k];
+        d.phi[i] = d.mass[i] / d.rho[i];
+    }
+}
+
+void launch_fin_frozen(const Dev &d, cudaStream_t s) {
+    static const int g = list_blocks((const void *)k_fin_frozen, LIST_BLOCK, 4);
+    k_fin_frozen<<<g, LIST_BLOCK, 0, s>>>(d);
 }
 
 // active segments -> list (warp-ballot compaction); counter zeroed first

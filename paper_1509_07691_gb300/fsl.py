@@ -24,6 +24,7 @@ BGK, TRT = 0, 1
 CURV_LSQR, CURV_FD, CURV_NONE, CURV_MLP = 0, 1, 2, 3
 F32, F16_OFS, BF16_OFS = 0, 1, 2
 WHERE_NONE, WHERE_HOST, WHERE_DEVICE = 0, 1, 2
+JAC_STRIDE = 344  # curvature Jacobian row: 7x7x7 window slots, then theta
 GEOMETRY_KINDS = {"sphere": 0, "mode2": 1, "cap": 2, "two_spheres": 3, "pool": 4, "plane": 5}
 Q = 19
 
@@ -77,6 +78,15 @@ _SIGNATURES = {
                            [ctypes.c_void_p] * 3),
     "fsl_mlp_pack": (ctypes.c_int, [ctypes.c_void_p] * 3),
     "fsl_mlp_attach": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
+    "fsl_adjoint_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int,
+                                                     ctypes.c_int]),
+    "fsl_set_surface": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]),
+    "fsl_window_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_size_t]),
+    "fsl_window_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)] + [ctypes.c_void_p] * 3),
+    "fsl_kappa_jacobian": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int] +
+                           [ctypes.c_void_p] * 3 + [ctypes.POINTER(ctypes.c_int)]),
     "fsl_parity": (ctypes.c_int, [ctypes.c_void_p]),
     "fsl_status": (ctypes.c_int, [ctypes.c_void_p]),
     "fsl_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -272,6 +282,84 @@ class Sim:
                     mass=self.mass.double().cpu().numpy(), phi=self.phi.double().cpu().numpy(),
                     kappa=self.kappa.double().cpu().numpy())
 
+    # -- adjoint windows (frozen cell types) ----------------------------------------
+    def set_surface(self, sigma: float, theta: float):
+        """New surface tension and contact angle (radians) for the next steps."""
+        check(lib().fsl_set_surface(self.ctx, float(sigma), float(theta)), "fsl_set_surface")
+        self.p.sigma, self.p.theta = float(sigma), float(theta)
+
+    def interface_count(self) -> int:
+        return int(self.stats()[1])
+
+    def _adj_workspace(self, window, ckpt_every, max_interface, slot="_adj_ws"):
+        nbytes = lib().fsl_adjoint_workspace_size(ctypes.byref(self.p), int(window), int(ckpt_every),
+                                                  int(max_interface))
+        if nbytes == 0:
+            raise FslError("fsl_adjoint_workspace_size: invalid arguments")
+        ws = getattr(self, slot, None)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            setattr(self, slot, ws)
+        return ws, nbytes
+
+    def window_forward(self, window: int, ckpt_every: int = 10, max_interface: int | None = None):
+        """`window` steps with frozen cell types, checkpoints every `ckpt_every`."""
+        if max_interface is None:
+            max_interface = 2 * self.interface_count() + 1024
+        ws, nbytes = self._adj_workspace(window, ckpt_every, max_interface)
+        check(lib().fsl_window_forward(self.ctx, int(window), int(ckpt_every), int(max_interface),
+                                       ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel())),
+              "fsl_window_forward")
+        self._adj_window = (int(window), int(ckpt_every), int(max_interface))
+
+    def window_adjoint(self, dL_dphi: torch.Tensor, inputs: bool = False):
+        """dL/dsigma, dL/dtheta of the last window from dL/dphi at its end; with
+        inputs=True also dL/dphi, dL/dm and dL/df' at its start."""
+        g = dL_dphi.to(device=self.device, dtype=torch.float32).contiguous()
+        assert g.numel() == self.N
+        outs = [None, None, None]
+        if inputs:
+            outs = [torch.zeros(self.shape, dtype=torch.float32, device=self.device),
+                    torch.zeros(self.shape, dtype=torch.float32, device=self.device),
+                    torch.zeros((Q,) + self.shape, dtype=torch.float32, device=self.device)]
+        ds, dt = ctypes.c_double(), ctypes.c_double()
+        torch.cuda.current_stream(self.device).synchronize()
+        check(lib().fsl_window_adjoint(self.ctx, ctypes.c_void_p(g.data_ptr()), ctypes.byref(ds), ctypes.byref(dt),
+                                       *[_ptr(t) for t in outs]), "fsl_window_adjoint")
+        if inputs:
+            return ds.value, dt.value, outs[0], outs[1], outs[2]
+        return ds.value, dt.value
+
+    def kappa_jacobian(self, max_interface: int | None = None):
+        """(jac [n, JAC_STRIDE], cells [n], kappa [n]) of the current state."""
+        if max_interface is None:
+            max_interface = self.interface_count() + 64
+        ws, nbytes = self._adj_workspace(1, 1, max_interface, slot="_jac_ws")
+        jac = torch.zeros((max_interface, JAC_STRIDE), dtype=torch.float32, device=self.device)
+        cells = torch.zeros(max_interface, dtype=torch.int32, device=self.device)
+        kap = torch.zeros(max_interface, dtype=torch.float32, device=self.device)
+        n = ctypes.c_int()
+        check(lib().fsl_kappa_jacobian(self.ctx, ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+                                       int(max_interface), _ptr(jac), _ptr(cells), _ptr(kap), ctypes.byref(n)),
+              "fsl_kappa_jacobian")
+        return jac[: n.value], cells[: n.value], kap[: n.value]
+
+    def snapshot(self) -> dict:
+        """Device copy of the current state (PDFs, types, mass, fill level)."""
+        torch.cuda.synchronize(self.device)
+        return dict(f=self.f_current().clone(), flags=self.flags[0].clone(), mass=self.mass.clone(),
+                    phi=self.phi.clone())
+
+    def restore(self, snap: dict):
+        """Put a snapshot back as the current state (lists rebuilt by refresh)."""
+        torch.cuda.synchronize(self.device)
+        self.f_current().copy_(snap["f"])
+        self.flags[0].copy_(snap["flags"])
+        self.mass.copy_(snap["mass"])
+        self.phi.copy_(snap["phi"])
+        torch.cuda.synchronize(self.device)
+        self.refresh()
+
     def close(self):
         if getattr(self, "ctx", None):
             lib().fsl_destroy(self.ctx)
@@ -355,3 +443,26 @@ def mlp_stencils(params: dict, sub=8, noise=1e-3, noise_seed=0, device="cuda", s
                                  int(sub), float(noise), int(noise_seed), _ptr(X), _ptr(target),
                                  _stream_handle(stream)), "fsl_mlp_stencils")
     return X, target
+
+
+class FslStepWindow(torch.autograd.Function):
+    """phi after `window` steps with frozen cell types, as a function of
+    surface = tensor([sigma, theta]) (float64, theta in radians).  The forward
+    pass runs fsl_window_forward from the simulation's current state (the
+    caller puts the start state in place, e.g. Sim.restore); the backward pass
+    is fsl_window_adjoint (checkpointed recomputation, hand-written reverse
+    kernels)."""
+
+    @staticmethod
+    def forward(ctx, surface, sim, window, ckpt_every=10):
+        s = surface.detach().cpu().double()
+        sim.set_surface(float(s[0]), float(s[1]))
+        sim.window_forward(int(window), int(ckpt_every))
+        ctx.sim = sim
+        torch.cuda.synchronize(sim.device)
+        return sim.phi.clone()
+
+    @staticmethod
+    def backward(ctx, grad_phi):
+        ds, dt = ctx.sim.window_adjoint(grad_phi)
+        return torch.tensor([ds, dt], dtype=torch.float64), None, None, None
