@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--mlp-train", type=int, default=10_000_000, help="training stencils of the learned curvature")
     ap.add_argument("--mlp-epochs", type=int, default=2)
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint-window section (one evaluation, no checks) and print it")
     return ap.parse_args()
 
 
@@ -424,6 +426,135 @@ def learned_curvature(F, S, stream, flush, peaks, seed, n_train, epochs, steps):
     return out
 
 
+def adjoint_window(F, S, stream, seed, window=50, ckpt=10, reps=5, warm=2, checks=True):
+    """Differentiation form: sessile droplet 64^3 (R 16, walls), windows of 50
+    steps with frozen cell types and a checkpoint every 10 steps.  Loss: L2 of
+    the interface fill levels against the window run at theta 70 deg, sigma
+    3e-4; gradient at theta 90 deg, sigma 2e-4 by the reverse pass; timing of
+    the forward window and of the reverse pass; L-BFGS fit through the
+    autograd Function from the start point."""
+    import torch
+    from scipy.optimize import minimize
+    w = S.workload("sessile64", seed=seed)
+    P, sim, phi0, obs = make_sim(F, w, "lsqr", "f32", stream)
+    start = sim.snapshot()
+    th0, s0 = math.radians(90.0), 2e-4
+    th1, s1 = math.radians(70.0), 3e-4
+    sim.set_surface(s1, th1)
+    sim.window_forward(window, ckpt)
+    torch.cuda.synchronize()
+    tgt = sim.phi.clone()
+    ifc = (sim.flags_current() & F.TYPE_MASK) == F.INTERFACE
+    n_if = int(ifc.sum())
+    n_fluid = int(((sim.flags_current() & F.TYPE_MASK) & (F.LIQUID | F.INTERFACE) != 0).sum())
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def evaluate(theta, sigma, grad=False):
+        sim.restore(start)
+        sim.set_surface(sigma, theta)
+        e[0].record(stream)
+        sim.window_forward(window, ckpt)
+        e[1].record(stream)
+        d = torch.where(ifc, sim.phi - tgt, torch.zeros_like(tgt))
+        L = float(torch.sum(d.double() ** 2))
+        if not grad:
+            return L, e[0].elapsed_time(e[1])
+        g = 2.0 * d
+        torch.cuda.synchronize()
+        e[1].record(stream)
+        ds, dt = sim.window_adjoint(g)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        return L, ds, dt, e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+
+    for _ in range(warm):
+        evaluate(th0, s0, grad=True)
+    fwd, bwd = [], []
+    for _ in range(reps):
+        L, ds, dt, tf, tb = evaluate(th0, s0, grad=True)
+        fwd.append(tf)
+        bwd.append(tb)
+    tfw, tbw = float(np.median(fwd)), float(np.median(bwd))
+    out = {"workload": "sessile64", "grid": list(w["shape"][::-1]), "window": window, "checkpoint_every": ckpt,
+           "fluid_cells": n_fluid, "interface_cells": n_if, "target": {"theta_deg": 70.0, "sigma": s1},
+           "start": {"theta_deg": 90.0, "sigma": s0}, "loss": L, "dL_dsigma": ds, "dL_dtheta": dt,
+           "forward_ms": tfw, "reverse_ms": tbw, "reverse_over_forward": tbw / tfw,
+           "forward_mlups": n_fluid * window / (tfw * 1e-3) / 1e6,
+           "reverse_mlups": n_fluid * window / (tbw * 1e-3) / 1e6}
+    if not checks:
+        sim.close()
+        return out
+    hs, ht = 5e-2 * s0, 1e-2
+    fd_s = (evaluate(th0, s0 + hs)[0] - evaluate(th0, s0 - hs)[0]) / (2 * hs)
+    fd_t = (evaluate(th0 + ht, s0)[0] - evaluate(th0 - ht, s0)[0]) / (2 * ht)
+    scale = np.array([1e-4, math.radians(10.0)])
+    nev = [0]
+
+    def fun(xs):
+        surface = torch.tensor(xs * scale, dtype=torch.float64, requires_grad=True)
+        sim.restore(start)
+        phi = F.FslStepWindow.apply(surface, sim, window, ckpt)
+        loss = torch.sum(torch.where(ifc, phi - tgt, torch.zeros_like(tgt)).double() ** 2)
+        loss.backward()
+        nev[0] += 1
+        return float(loss.detach()), surface.grad.numpy() * scale
+
+    t0 = time.perf_counter()
+    res = minimize(fun, np.array([s0, th0]) / scale, jac=True, method="L-BFGS-B", bounds=[(0.5, 6.0), (3.0, 15.0)],
+                   options=dict(maxiter=60, ftol=1e-14, gtol=1e-12))
+    fit_s = time.perf_counter() - t0
+    sf, tf_ = res.x * scale
+    out.update({"fp32_differences": {"dL_dsigma": fd_s, "dL_dtheta": fd_t, "step_sigma": hs, "step_theta_rad": ht,
+                                "rel_err_sigma": abs(ds - fd_s) / abs(fd_s), "rel_err_theta": abs(dt - fd_t) / abs(fd_t)},
+           "fit": {"theta_deg": math.degrees(tf_), "sigma": sf, "theta_err_deg": math.degrees(tf_) - 70.0,
+                   "sigma_rel_err": sf / s1 - 1.0, "evaluations": nev[0], "seconds": fit_s,
+                   "method": "L-BFGS-B on (sigma/1e-4, theta/10 deg), gradients from the reverse pass"}})
+    sim.close()
+    del sim, phi0, obs, start
+    torch.cuda.empty_cache()
+    return out
+
+
+def _oracle_window_loss(args):
+    """One FP64 oracle window (frozen types) of the sessile droplet; returns
+    phi at its end, or the L2 loss to `target` on interface cells."""
+    name, theta, sigma, window, target = args
+    import oracle as orc
+    from paper_1509_07691_gb300 import synthetic as S
+    w = S.workload(name)
+    g = w["geometry"]
+    phi = orc.fill(orc.geom("cap", c=g["c"], R=g["R"], zw=g["zw"], sub=16), w["shape"])
+    obs = S.obstacle_mask(w["shape"], w["walls"])
+    P = orc.params(w["shape"], collision=1, tau=w["tau"], sigma=sigma, theta=theta, frozen=1)
+    st = orc.init_state(P, phi, obs)
+    for _ in range(window):
+        st, _, _, _ = orc.step(P, st)
+    if target is None:
+        return st.phi, st.flags
+    m = st.flags == 2
+    return float(np.sum((st.phi[m] - target[m]) ** 2))
+
+
+def adjoint_reference(window=50):
+    """FP64 reference gradient of the adjoint section's loss: central
+    differences (h = 1e-4 relative) of the oracle's frozen-type window, the
+    target made by the oracle itself; windows run in a spawn pool."""
+    import multiprocessing as mp
+    th0, s0 = math.radians(90.0), 2e-4
+    t0 = time.perf_counter()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        target, _ = pool.apply(_oracle_window_loss, (("sessile64", math.radians(70.0), 3e-4, window, None),))
+    hs, ht = 1e-4 * s0, 1e-4
+    jobs = [("sessile64", th0, s0 + hs, window, target), ("sessile64", th0, s0 - hs, window, target),
+            ("sessile64", th0 + ht, s0, window, target), ("sessile64", th0 - ht, s0, window, target)]
+    with ctx.Pool(4) as pool:
+        Ls = pool.map(_oracle_window_loss, jobs)
+    return {"dL_dsigma": (Ls[0] - Ls[1]) / (2 * hs), "dL_dtheta": (Ls[2] - Ls[3]) / (2 * ht), "step_sigma": hs,
+            "step_theta_rad": ht, "seconds": time.perf_counter() - t0, "processes": 4,
+            "method": "central differences of the FP64 oracle window (frozen types), own target"}
+
+
 def run_fsl(args):
     import torch
     ws, rank, local = dist_info()
@@ -554,11 +685,17 @@ def run_fsl(args):
                                min(args.steps, 100))
         held = lc.pop("heldout")
         line["learned_curvature"] = lc
+        line["adjoint"] = adjoint_window(F, S, stream, S.SEED + rank)
     if gs is not None:
         line["cpu_baseline"] = oracle_sample(w, args.cpu_seconds, gpu_state=gs)
         line["kappa_err_vs_fp64"] = line["cpu_baseline"].pop("kappa_check")
         if not args.no_side:
             line["learned_curvature"]["heldout_kappa_rel_err"] = heldout_errors(held)
+            ref = adjoint_reference()
+            adj = line["adjoint"]
+            ref["rel_err_sigma"] = abs(adj["dL_dsigma"] - ref["dL_dsigma"]) / abs(ref["dL_dsigma"])
+            ref["rel_err_theta"] = abs(adj["dL_dtheta"] - ref["dL_dtheta"]) / abs(ref["dL_dtheta"])
+            adj["fp64_reference"] = ref
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -569,6 +706,14 @@ def run_fsl(args):
 
 def main():
     args = parse()
+    if args.adjoint_only:
+        import torch
+        from paper_1509_07691_gb300 import build, synthetic as S
+        build.build()
+        from paper_1509_07691_gb300 import fsl as F
+        stream = torch.cuda.current_stream()
+        print(json.dumps({"adjoint": adjoint_window(F, S, stream, S.SEED, reps=1, warm=0, checks=False)}))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
