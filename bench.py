@@ -438,6 +438,8 @@ def adjoint_window(F, S, stream, seed, window=50, ckpt=10, reps=5, warm=2, check
     w = S.workload("sessile64", seed=seed)
     P, sim, phi0, obs = make_sim(F, w, "lsqr", "f32", stream)
     start = sim.snapshot()
+    sim.curvature(F.CURV_LSQR, torch.empty_like(sim.kappa))
+    fp64_cells = int(sim.stats()[6])
     th0, s0 = math.radians(90.0), 2e-4
     th1, s1 = math.radians(70.0), 3e-4
     sim.set_surface(s1, th1)
@@ -476,7 +478,8 @@ def adjoint_window(F, S, stream, seed, window=50, ckpt=10, reps=5, warm=2, check
         bwd.append(tb)
     tfw, tbw = float(np.median(fwd)), float(np.median(bwd))
     out = {"workload": "sessile64", "grid": list(w["shape"][::-1]), "window": window, "checkpoint_every": ckpt,
-           "fluid_cells": n_fluid, "interface_cells": n_if, "target": {"theta_deg": 70.0, "sigma": s1},
+           "fluid_cells": n_fluid, "interface_cells": n_if, "lsqr_fp64_cells_at_start": fp64_cells,
+           "target": {"theta_deg": 70.0, "sigma": s1},
            "start": {"theta_deg": 90.0, "sigma": s0}, "loss": L, "dL_dsigma": ds, "dL_dtheta": dt,
            "forward_ms": tfw, "reverse_ms": tbw, "reverse_over_forward": tbw / tfw,
            "forward_mlups": n_fluid * window / (tfw * 1e-3) / 1e6,

@@ -21,6 +21,7 @@ struct Adj {
     float *jac;          // [cap][JAC_STRIDE]
     float *jval;         // [cap] kappa value of the Jacobian pass
     int *dlist;          // wlist positions whose Jacobian is redone in FP64
+    float4 *nj;          // [cap][125] d(n, a)/dphi over the 5x5x5 window of each interface cell
     const float *fb_in;  // adjoint of the post-collision PDFs at t+1 [19 N]
     float *fb_out;       // adjoint of the post-collision PDFs at t   [19 N]
     float *gb;           // adjoint of the pre-collision PDFs of step t [19 N]
@@ -44,9 +45,12 @@ void launch_adjoint_seed(const Dev &d, const Adj &a, const float *dL_dphi, cudaS
 void launch_adjoint_step(const Dev &d, const Adj &a, cudaStream_t s);
 // Curvature Jacobian rows of the window's interface cells at the state in d.
 void launch_kappa_jacobian(const Dev &d, const Adj &a, cudaStream_t s);
-// Window bookkeeping: copy the interface list and the active segments of the
-// step-parity view `src` into the window's own buffers (counts, list, index).
-void launch_window_setup(const Dev &src, int *wcounts, int *wlist, int *widx, int *wseg, cudaStream_t s);
+// Window bookkeeping: the interface cells of the view `src` in cell-index
+// order (list and cell -> position index) and a copy of its active segments,
+// into the window's own buffers; scratch holds window_scratch_ints(N) ints.
+int window_scratch_ints(long long N);
+void launch_window_setup(const Dev &src, int *wcounts, int *wlist, int *widx, int *wseg, int *scratch,
+                         cudaStream_t s);
 // Copy the window's interface list back into the step-parity view `dst`.
 void launch_window_finish(const Dev &dst, const int *wcounts, const int *wlist, cudaStream_t s);
 

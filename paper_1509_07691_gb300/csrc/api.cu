@@ -207,7 +207,7 @@ int record_graph(fsl_ctx *c, int parity) {
 constexpr int ADJ_MAX_PARTIALS = 4096;
 
 struct AdjLayout {
-    size_t wcounts, wlist, widx, wseg, ckpt, slot, kn, fb0, fb1, gb, mb, pb, kb, jac, jval, dlist, part, acc, total;
+    size_t wcounts, wlist, widx, wseg, wscr, ckpt, slot, kn, fb0, fb1, gb, mb, pb, kb, jac, jval, dlist, nj, part, acc, total;
     size_t state_bytes;  // one (f', m, phi) record
     size_t kn_bytes;     // one (kappa, normal) record
     int nseg_ckpt;
@@ -224,6 +224,7 @@ AdjLayout adj_layout(const fsl_params &p, int W, int K, int cap) {
     A.wlist = o; o += up(N * sizeof(int));
     A.widx = o; o += up(N * sizeof(int));
     A.wseg = o; o += up(nseg_of(p) * sizeof(int));
+    A.wscr = o; o += up((size_t)window_scratch_ints((long long)N) * sizeof(int));
     A.ckpt = o; o += (size_t)A.nseg_ckpt * A.state_bytes;
     A.slot = o; o += (size_t)K * A.state_bytes;
     A.kn = o; o += (size_t)K * A.kn_bytes;
@@ -236,6 +237,7 @@ AdjLayout adj_layout(const fsl_params &p, int W, int K, int cap) {
     A.jac = o; o += up((size_t)cap * JAC_STRIDE * sizeof(float));
     A.jval = o; o += up((size_t)cap * sizeof(float));
     A.dlist = o; o += up((size_t)cap * sizeof(int));
+    A.nj = o; o += up((size_t)cap * 125 * sizeof(float4));
     A.part = o; o += up(2 * ADJ_MAX_PARTIALS * sizeof(double));
     A.acc = o; o += up(2 * sizeof(double));
     A.total = o;
@@ -283,6 +285,7 @@ Adj adj_args(char *ws, const AdjLayout &A, int cap) {
     a.jac = reinterpret_cast<float *>(ws + A.jac);
     a.jval = reinterpret_cast<float *>(ws + A.jval);
     a.dlist = reinterpret_cast<int *>(ws + A.dlist);
+    a.nj = reinterpret_cast<float4 *>(ws + A.nj);
     a.gb = reinterpret_cast<float *>(ws + A.gb);
     a.mb = reinterpret_cast<float *>(ws + A.mb);
     a.pb = reinterpret_cast<float *>(ws + A.pb);
@@ -300,7 +303,7 @@ int window_setup(fsl_ctx *c, char *ws, const AdjLayout &A, int *n_out) {
     int *wc = reinterpret_cast<int *>(ws + A.wcounts);
     CK(cudaMemsetAsync(wc, 0, C_NCOUNT * sizeof(int), c->stream));
     launch_window_setup(src, wc, reinterpret_cast<int *>(ws + A.wlist), reinterpret_cast<int *>(ws + A.widx),
-                        reinterpret_cast<int *>(ws + A.wseg), c->stream);
+                        reinterpret_cast<int *>(ws + A.wseg), reinterpret_cast<int *>(ws + A.wscr), c->stream);
     CK(cudaMemcpyAsync(c->host_count, wc + C_IF0, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     *n_out = *c->host_count;
@@ -650,6 +653,8 @@ int fsl_kappa_jacobian(fsl_ctx *c, void *adj_ws, size_t adj_bytes, int max_inter
     a.jval = kappa_out;
     Dev d = window_dev(c, ws, A);
     d.phi = c->fields.phi;
+    d.normal = c->base.normal;
+    launch_normals(d, c->stream);  // the fit reads the normals of this state
     launch_kappa_jacobian(d, a, c->stream);
     CK(cudaMemcpyAsync(cells_out, a.wlist, (size_t)nif * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));

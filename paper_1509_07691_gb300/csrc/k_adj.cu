@@ -51,20 +51,76 @@ int adj_blocks() {
 }
 
 // ---- window bookkeeping ---------------------------------------------------------
-__global__ void k_window_setup(Dev d, int *wcounts, int *wlist, int *widx, int *wseg) {
-    int cnt[2];
-    block_counts<2>(d.counts, {d.cif, C_SEG}, cnt);
+// The window's interface list is built from the cell types in cell-index
+// order (block counts, one scan, ordered writes), so that every reduction
+// over it runs in the same order whatever the order of the step's own list.
+constexpr int WIN_BLOCK = 1024;
+
+__global__ void __launch_bounds__(WIN_BLOCK) k_window_count(Dev d, int *bcount) {
+    const long long i = (long long)blockIdx.x * WIN_BLOCK + threadIdx.x;
+    const bool p = i < d.N && (d.flags[i] & T_MASK) == T_IF;
+    const int c = __syncthreads_count(p);
+    if (threadIdx.x == 0) bcount[blockIdx.x] = c;
+}
+
+// exclusive scan of the nb block counts (one block); the total into wcounts
+__global__ void __launch_bounds__(WIN_BLOCK) k_window_scan(int *bcount, int nb, int *wcounts) {
+    __shared__ int part[WIN_BLOCK];
+    const int per = (nb + WIN_BLOCK - 1) / WIN_BLOCK;
+    const int b0 = threadIdx.x * per, b1 = min(nb, b0 + per);
+    int sum = 0;
+    for (int b = b0; b < b1; ++b) sum += bcount[b];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int t = 0; t < WIN_BLOCK; ++t) {
+            const int v = part[t];
+            part[t] = run;
+            run += v;
+        }
+        wcounts[C_IF0] = run;
+    }
+    __syncthreads();
+    int run = part[threadIdx.x];
+    for (int b = b0; b < b1; ++b) {
+        const int v = bcount[b];
+        bcount[b] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(WIN_BLOCK) k_window_write(Dev d, const int *boff, int *wlist, int *widx) {
+    __shared__ int wsum[WIN_BLOCK / 32];
+    const long long i = (long long)blockIdx.x * WIN_BLOCK + threadIdx.x;
+    const bool p = i < d.N && (d.flags[i] & T_MASK) == T_IF;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned m = __ballot_sync(0xffffffffu, p);
+    if (lane == 0) wsum[warp] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < WIN_BLOCK / 32; ++w) {
+            const int v = wsum[w];
+            wsum[w] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    if (p) {
+        const int pos = boff[blockIdx.x] + wsum[warp] + __popc(m & ((1u << lane) - 1u));
+        wlist[pos] = (int)i;
+        widx[i] = pos;
+    }
+}
+
+// active segments of the step's view (their order does not matter)
+__global__ void k_window_segs(Dev d, int *wcounts, int *wseg) {
+    int cnt[1];
+    block_counts<1>(d.counts, {C_SEG}, cnt);
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    if (tid == 0) {
-        wcounts[C_IF0] = cnt[0];
-        wcounts[C_SEG] = cnt[1];
-    }
-    for (int k = tid; k < cnt[0]; k += nth) {
-        const int i = d.iflist[k];
-        wlist[k] = i;
-        widx[i] = k;
-    }
-    for (int k = tid; k < cnt[1]; k += nth) wseg[k] = d.seg_list[k];
+    if (tid == 0) wcounts[C_SEG] = cnt[0];
+    for (int k = tid; k < cnt[0]; k += nth) wseg[k] = d.seg_list[k];
 }
 
 __global__ void k_window_finish(Dev d, const int *wcounts, const int *wlist) {
@@ -75,10 +131,17 @@ __global__ void k_window_finish(Dev d, const int *wcounts, const int *wlist) {
     for (int k = tid; k < cnt[0]; k += nth) d.iflist[k] = wlist[k];
 }
 
-void launch_window_setup(const Dev &src, int *wcounts, int *wlist, int *widx, int *wseg, cudaStream_t s) {
+int window_scratch_ints(long long N) { return (int)((N + WIN_BLOCK - 1) / WIN_BLOCK); }
+
+void launch_window_setup(const Dev &src, int *wcounts, int *wlist, int *widx, int *wseg, int *scratch,
+                         cudaStream_t s) {
+    const int nb = window_scratch_ints(src.N);
     cudaMemsetAsync(widx, 0xff, (size_t)src.N * sizeof(int), s);
-    static const int g = list_blocks((const void *)k_window_setup, 256, 2);
-    k_window_setup<<<g, 256, 0, s>>>(src, wcounts, wlist, widx, wseg);
+    k_window_count<<<nb, WIN_BLOCK, 0, s>>>(src, scratch);
+    k_window_scan<<<1, WIN_BLOCK, 0, s>>>(scratch, nb, wcounts);
+    k_window_write<<<nb, WIN_BLOCK, 0, s>>>(src, scratch, wlist, widx);
+    static const int g = list_blocks((const void *)k_window_segs, 256, 2);
+    k_window_segs<<<g, 256, 0, s>>>(src, wcounts, wseg);
 }
 
 void launch_window_finish(const Dev &dst, const int *wcounts, const int *wlist, cudaStream_t s) {
@@ -159,23 +222,37 @@ __device__ __forceinline__ void collide_adj(const float g[Q], const float fb[Q],
 }
 
 // ---- curvature Jacobian ---------------------------------------------------------
-// Accessor of curv_common.cuh over the 7x7x7 window of fill levels and flags
-// held in shared memory, with one seeded direction: the fill level of window
-// slot `seed`, or theta (seed == JAC_CELLS).  Normals and PLIC offsets of the
-// neighbours are recomputed in Dual<float> (as k_normals computes them in
-// float) and handed to the fit in its scalar type T.
-__device__ __forceinline__ int jac_slot(int dx, int dy, int dz) { return (dz + 3) * 49 + (dy + 3) * 7 + (dx + 3); }
+// kappa_x depends on the fill levels through the PLIC normal and offset
+// (n_j, a_j) of the interface cells j of its 3x3x3 neighbourhood, and on
+// theta through the contact rows.  Two stages:
+//   k_normal_jac  per interface cell j: d(n_j, a_j)/dphi over the 5x5x5
+//                 window around j (Parker-Youngs stencil, obstacle reflection,
+//                 PLIC offset by the implicit function theorem); dual numbers
+//                 through the same code as k_normals, one seed per lane
+//   k_kappa_jac   per interface cell x: dkappa_x/d(n_j, a_j) for the four
+//                 inputs of each interface cell j of the 3x3x3 neighbourhood
+//                 and dkappa_x/dtheta (dual numbers through lsqr_core with the
+//                 stored normals as values, one seed per lane), then the
+//                 chain rule dkappa_x/dphi_y = sum_j sum_c
+//                 dkappa_x/d(n_j,a_j)_c d(n_j,a_j)_c/dphi_y
+//                 into the row of x (7x7x7 window slots, theta last).
+// A cell whose FP32 fit is ill conditioned (cond^2 above fp64_cond, as
+// k_lsqr_slow decides) is listed and its second stage redone in Dual<double>.
 
+// Window of half-width R (fill levels and flags) in shared memory, with one
+// seeded fill level (window slot `seed`).
+template <int R>
 struct WinAcc {
+    static constexpr int W = 2 * R + 1;
     const float *phi;
     const uint8_t *fl;
     int seed;
-    double ct, st;
     int iters;
 
-    __device__ __forceinline__ uint8_t flag(int dx, int dy, int dz) const { return fl[jac_slot(dx, dy, dz)]; }
+    __device__ __forceinline__ static int slot(int dx, int dy, int dz) { return ((dz + R) * W + (dy + R)) * W + (dx + R); }
+    __device__ __forceinline__ uint8_t flag(int dx, int dy, int dz) const { return fl[slot(dx, dy, dz)]; }
     __device__ __forceinline__ Dual<float> phi_d(int dx, int dy, int dz) const {
-        const int s = jac_slot(dx, dy, dz);
+        const int s = slot(dx, dy, dz);
         return Dual<float>(phi[s], s == seed ? 1.0f : 0.0f, 0);
     }
     __device__ __forceinline__ Dual<float> phi_ext(int dx, int dy, int dz) const {
@@ -183,97 +260,189 @@ struct WinAcc {
         return reflect_value<Dual<float>>([&](int a, int b, int c) { return flag(dx + a, dy + b, dz + c); },
                                           [&](int a, int b, int c) { return phi_d(dx + a, dy + b, dz + c); });
     }
+    // normal and PLIC offset of the centre cell, as k_normals computes them
+    __device__ __forceinline__ bool centre_normal(Dual<float> n[3], Dual<float> &a) const {
+        using DF = Dual<float>;
+        if (flag(0, 0, 0) & B_NEAR)
+            parker_youngs<DF>([&](int ex, int ey, int ez) { return phi_ext(ex, ey, ez); }, n);
+        else
+            parker_youngs<DF>([&](int ex, int ey, int ez) { return phi_d(ex, ey, ez); }, n);
+        return unit_normal_offset<DF>(n, phi_d(0, 0, 0), iters, a);
+    }
+};
+
+constexpr int JAC_WARPS = 4;
+constexpr int NJ_CELLS = 125;  // 5x5x5 window of d(n_j, a_j)/dphi
+
+__global__ void __launch_bounds__(JAC_WARPS * 32) k_normal_jac(Dev d, Adj a) {
+    __shared__ float sphi[JAC_WARPS][NJ_CELLS];
+    __shared__ uint8_t sfl[JAC_WARPS][NJ_CELLS + 3];
+    __shared__ uint8_t sseed[JAC_WARPS][NJ_CELLS + 3];
+    int cnt[1];
+    block_counts<1>(d.counts, {C_IF0}, cnt);
+    const int n = min(cnt[0], a.cap);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int k = gw; k < n; k += nwarps) {
+        const int i = a.wlist[k];
+        int x, y, z;
+        cell_coords(d, i, x, y, z);
+        float4 *row = a.nj + (size_t)k * NJ_CELLS;
+        for (int sl = lane; sl < NJ_CELLS; sl += 32) {
+            const int j = nbr_index(d, x, y, z, sl % 5 - 2, (sl / 5) % 5 - 2, sl / 25 - 2);
+            sphi[w][sl] = d.phi[j];
+            sfl[w][sl] = d.flags[j];
+            row[sl] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        // seeds: interface cells of the 3x3x3 stencil, of the 5x5x5 window
+        // at a cell next to an obstacle (reflected fill levels)
+        const bool near = (sfl[w][NJ_CELLS / 2] & B_NEAR) != 0;
+        int ns = 0;
+        for (int base = 0; base < NJ_CELLS; base += 32) {
+            const int sl = base + lane;
+            const int ox = sl % 5 - 2, oy = (sl / 5) % 5 - 2, oz = sl / 25 - 2;
+            const bool inner = ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1;
+            const bool p = sl < NJ_CELLS && (sfl[w][sl] & T_IF) && (near || inner);
+            const unsigned m = __ballot_sync(0xffffffffu, p);
+            if (p) sseed[w][ns + __popc(m & ((1u << lane) - 1u))] = (uint8_t)sl;
+            ns += __popc(m);
+        }
+        __syncwarp();
+        for (int base = 0; base < ns; base += 32) {
+            const int idx = base + lane;
+            const WinAcc<2> acc{sphi[w], sfl[w], idx < ns ? (int)sseed[w][idx] : -1, d.plic_iters};
+            Dual<float> nv[3], av;
+            const bool ok = acc.centre_normal(nv, av);
+            if (ok && idx < ns) row[sseed[w][idx]] = make_float4(nv[0].d, nv[1].d, nv[2].d, av.d);
+        }
+        __syncwarp();
+    }
+}
+
+// Accessor of lsqr_core over the grid with the stored normals as values and
+// one seeded input: component c of (n_j, a_j) of the neighbour j at 3x3x3
+// slot sj, or theta.
+struct SeedAcc {
+    const Dev &d;
+    int x, y, z;
+    int sj, sc;
+    bool sth;
+    __device__ __forceinline__ uint8_t flag(int dx, int dy, int dz) const {
+        return d.flags[nbr_index(d, x, y, z, dx, dy, dz)];
+    }
     template <typename T>
     __device__ __forceinline__ bool normal(int dx, int dy, int dz, T n[3], T &a) const {
-        using DF = Dual<float>;
-        DF nv[3], af;
-        if (flag(dx, dy, dz) & B_NEAR)
-            parker_youngs<DF>([&](int ex, int ey, int ez) { return phi_ext(dx + ex, dy + ey, dz + ez); }, nv);
-        else
-            parker_youngs<DF>([&](int ex, int ey, int ez) { return phi_d(dx + ex, dy + ey, dz + ez); }, nv);
-        if (!unit_normal_offset<DF>(nv, phi_d(dx, dy, dz), iters, af)) return false;
         using S = typename scalar_of<T>::type;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) n[k] = T((S)nv[k].v, (S)nv[k].d, 0);
-        a = T((S)af.v, (S)af.d, 0);
+        const float4 q4 = d.normal[nbr_index(d, x, y, z, dx, dy, dz)];
+        if (q4.x == 0.f && q4.y == 0.f && q4.z == 0.f) return false;
+        const bool me = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1) == sj;
+        n[0] = T((S)q4.x, (me && sc == 0) ? S(1) : S(0), 0);
+        n[1] = T((S)q4.y, (me && sc == 1) ? S(1) : S(0), 0);
+        n[2] = T((S)q4.z, (me && sc == 2) ? S(1) : S(0), 0);
+        a = T((S)q4.w, (me && sc == 3) ? S(1) : S(0), 0);
         return true;
     }
     template <typename T>
     __device__ __forceinline__ void theta(T &c, T &s) const {
         using S = typename scalar_of<T>::type;
-        const bool sd = seed == JAC_CELLS;
-        c = T((S)ct, sd ? (S)(-st) : S(0), 0);
-        s = T((S)st, sd ? (S)ct : S(0), 0);
+        c = T((S)d.cos_theta_d, sth ? (S)(-d.sin_theta_d) : S(0), 0);
+        s = T((S)d.sin_theta_d, sth ? (S)d.cos_theta_d : S(0), 0);
     }
 };
 
-// One warp per interface cell of the window (FROM_LIST: the positions in
-// a.dlist, redone in Dual<double>).  The seeds are the interface cells of
-// the window (the only cells whose fill level varies with frozen types) and
-// theta; each lane evaluates kappa of the centre cell with its own seed and
-// stores the derivative in the cell's Jacobian row.  A cell whose FP32 fit is
-// ill conditioned (cond^2 above fp64_cond, as k_lsqr_slow decides) is listed
-// for the FP64 pass.
-constexpr int JAC_WARPS = 4;
+constexpr int KJ_SEEDS = 27 * 4 + 1;  // (n_j, a_j) of each 3x3x3 cell, theta
 
 template <typename T, bool FROM_LIST>
 __global__ void __launch_bounds__(JAC_WARPS * 32) k_kappa_jac(Dev d, Adj a) {
-    __shared__ float sphi[JAC_WARPS][JAC_CELLS];
-    __shared__ uint8_t sfl[JAC_WARPS][JAC_CELLS + 1];
-    __shared__ short sseed[JAC_WARPS][JAC_STRIDE];
+    __shared__ uint8_t sseed[JAC_WARPS][KJ_SEEDS + 3];
+    __shared__ float sK[JAC_WARPS][KJ_SEEDS + 3];
+    __shared__ int sidx[JAC_WARPS][27];  // window-list position of the 3x3x3 cells used, -1 otherwise
+    __shared__ int spos[JAC_WARPS][27];  // their first seed in sK
     int cnt[1];
     block_counts<1>(d.counts, {FROM_LIST ? C_ADJ64 : C_IF0}, cnt);
     const int n = FROM_LIST ? cnt[0] : min(cnt[0], a.cap);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-    float *wphi = sphi[w];
-    uint8_t *wfl = sfl[w];
-    short *wseed = sseed[w];
     for (int t = gw; t < n; t += nwarps) {
         const int k = FROM_LIST ? a.dlist[t] : t;
         const int i = a.wlist[k];
         int x, y, z;
         cell_coords(d, i, x, y, z);
-        for (int sl = lane; sl < JAC_CELLS; sl += 32) {
-            const int j = nbr_index(d, x, y, z, sl % 7 - 3, (sl / 7) % 7 - 3, sl / 49 - 3);
-            wphi[sl] = d.phi[j];
-            wfl[sl] = d.flags[j];
+        const uint8_t fi = d.flags[i];
+        // seeds: the four inputs of every interface cell of the 3x3x3
+        // neighbourhood with a nonzero normal, then theta
+        bool use = false;
+        int jdx = -1;
+        if (lane < 27) {
+            const int j = nbr_index(d, x, y, z, lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1);
+            const float4 q4 = d.normal[j];
+            use = (d.flags[j] & T_IF) && !(q4.x == 0.f && q4.y == 0.f && q4.z == 0.f);
+            jdx = use ? a.widx[j] : -1;
+            use = use && jdx >= 0 && jdx < a.cap;
         }
-        __syncwarp();
-        int ns = 0;
-        for (int base = 0; base < JAC_CELLS; base += 32) {
-            const int sl = base + lane;
-            const bool p = sl < JAC_CELLS && (wfl[sl] & T_IF);
-            const unsigned m = __ballot_sync(0xffffffffu, p);
-            if (p) wseed[ns + __popc(m & ((1u << lane) - 1u))] = (short)sl;
-            ns += __popc(m);
+        const unsigned m = __ballot_sync(0xffffffffu, use);
+        const int nu = __popc(m);
+        if (lane < 27) {
+            const int p = use ? 4 * __popc(m & ((1u << lane) - 1u)) : -1;
+            sidx[w][lane] = use ? jdx : -1;
+            spos[w][lane] = p;
+            if (use)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) sseed[w][p + c] = (uint8_t)(lane * 4 + c);
         }
-        if (lane == 0) wseed[ns] = (short)JAC_CELLS;
-        ++ns;
+        if (lane == 0) sseed[w][4 * nu] = (uint8_t)(27 * 4);
+        const int ns = 4 * nu + 1;
         __syncwarp();
         bool redo = false;
         for (int base = 0; base < ns; base += 32) {
             const int idx = base + lane;
-            const WinAcc acc{wphi, wfl, idx < ns ? (int)wseed[idx] : -1, d.cos_theta_d, d.sin_theta_d, d.plic_iters};
+            const int code = idx < ns ? (int)sseed[w][idx] : -1;
+            const SeedAcc acc{d, x, y, z, code >= 0 && code < 108 ? code >> 2 : -1, code & 3, code == 108};
             T cond;
-            const T kap = lsqr_core<T>(acc, wfl[JAC_CENTRE], cond);
+            const T kap = lsqr_core<T>(acc, fi, cond);
             if (!FROM_LIST && (float)(cond.v * cond.v) > d.fp64_cond) {
                 redo = true;  // same value on every lane
                 break;
             }
-            if (idx < ns) a.jac[(size_t)k * JAC_STRIDE + wseed[idx]] = (float)kap.d;
+            if (idx < ns) sK[w][idx] = (float)kap.d;
             if (base == 0 && lane == 0) a.jval[k] = (float)kap.v;
         }
-        if (redo && lane == 0) a.dlist[atomicAdd(d.counts + C_ADJ64, 1)] = k;
+        if (redo) {
+            if (lane == 0) a.dlist[atomicAdd(d.counts + C_ADJ64, 1)] = k;
+            __syncwarp();
+            continue;
+        }
+        __syncwarp();
+        // chain rule into the row of x
+        float *jrow = a.jac + (size_t)k * JAC_STRIDE;
+        for (int sl = lane; sl < JAC_CELLS; sl += 32) {
+            const int ox = sl % 7 - 3, oy = (sl / 7) % 7 - 3, oz = sl / 49 - 3;
+            if (!(d.flags[nbr_index(d, x, y, z, ox, oy, oz)] & T_IF)) continue;
+            float acc = 0.f;
+            for (int tj = 0; tj < 27; ++tj) {
+                const int jk = sidx[w][tj];
+                if (jk < 0) continue;
+                const int rx = ox - (tj % 3 - 1), ry = oy - ((tj / 3) % 3 - 1), rz = oz - (tj / 9 - 1);
+                if (rx < -2 || rx > 2 || ry < -2 || ry > 2 || rz < -2 || rz > 2) continue;
+                const float4 v = a.nj[(size_t)jk * NJ_CELLS + ((rz + 2) * 5 + (ry + 2)) * 5 + (rx + 2)];
+                const int p = spos[w][tj];
+                acc += sK[w][p] * v.x + sK[w][p + 1] * v.y + sK[w][p + 2] * v.z + sK[w][p + 3] * v.w;
+            }
+            jrow[sl] = acc;
+        }
+        if (lane == 0) jrow[JAC_CELLS] = sK[w][ns - 1];
         __syncwarp();
     }
     if (!FROM_LIST && blockIdx.x == 0 && threadIdx.x == 0 && cnt[0] > a.cap) set_status(d.status, FSL_ECAPACITY);
 }
 
 void launch_kappa_jacobian(const Dev &d, const Adj &a, cudaStream_t s) {
+    static const int gn = list_blocks((const void *)k_normal_jac, JAC_WARPS * 32, 4);
     static const int g = list_blocks((const void *)k_kappa_jac<Dual<float>, false>, JAC_WARPS * 32, 4);
     static const int g64 = list_blocks((const void *)k_kappa_jac<Dual<double>, true>, JAC_WARPS * 32, 1);
     cudaMemsetAsync(d.counts + C_ADJ64, 0, sizeof(int), s);
+    k_normal_jac<<<gn, JAC_WARPS * 32, 0, s>>>(d, a);
     k_kappa_jac<Dual<float>, false><<<g, JAC_WARPS * 32, 0, s>>>(d, a);
     k_kappa_jac<Dual<double>, true><<<g64, JAC_WARPS * 32, 0, s>>>(d, a);
 }
