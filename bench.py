@@ -558,6 +558,20 @@ def adjoint_reference(window=50):
             "method": "central differences of the FP64 oracle window (frozen types), own target"}
 
 
+def reduce_over_ranks(ms, n_fluid, device):
+    """Timed milliseconds (max over ranks) and fluid cells (sum over ranks) of
+    the default process group; the values themselves on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(n_fluid)
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([n_fluid], dtype=torch.float64, device=device)
+    dist.all_reduce(n)
+    return float(t.item()), float(n.item())
+
+
 def run_fsl(args):
     import torch
     ws, rank, local = dist_info()
@@ -596,16 +610,7 @@ def run_fsl(args):
     t0 = time.time()
     ms = time_steps(sim, args.steps, stream, flush)
     t1 = time.time()
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-        nf = torch.tensor([n_fluid], dtype=torch.float64, device="cuda")
-        dist.all_reduce(nf)
-        total_fluid = float(nf.item())
-    else:
-        total_fluid = float(n_fluid)
+    ms, total_fluid = reduce_over_ranks(ms, n_fluid, "cuda")
     ms_per_step = ms / args.steps
     value = total_fluid * args.steps / (ms * 1e-3) / 1e6
     mass_end = sim.mass_total()
