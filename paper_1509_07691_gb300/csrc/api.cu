@@ -153,6 +153,8 @@ Dev dev_for(const fsl_ctx *c, int parity) {
     d.iflist_next = lists[parity ^ 1];
     d.cif = C_IF0 + parity;
     d.cif_next = C_IF0 + (parity ^ 1);
+    d.cdirty = C_SEGD0 + parity;
+    d.cdirty_next = C_SEGD0 + (parity ^ 1);
     return d;
 }
 
@@ -271,6 +273,8 @@ Dev window_dev(const fsl_ctx *c, char *ws, const AdjLayout &A) {
     d.iflist_next = nullptr;
     d.cif = C_IF0;
     d.cif_next = C_IF1;
+    d.cdirty = C_SEGD0;
+    d.cdirty_next = C_SEGD1;
     d.seg_list = reinterpret_cast<int *>(ws + A.wseg);
     d.frozen = 1;
     return d;

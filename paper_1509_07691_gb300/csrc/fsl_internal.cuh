@@ -46,9 +46,11 @@ enum : uint8_t {
 };
 
 // device counters in the workspace: interface-list lengths of the two list
-// buffers, conversion lists, FP64 LSQR re-solves, active segments
+// buffers, conversion lists, FP64 LSQR re-solves, active segments, and the
+// two "segment set changed" flags (one per step parity: a step sets its own,
+// clears the next step's, and rebuilds the segment list only if it is set)
 enum { C_IF0 = 0, C_IF1 = 1, C_FILL = 2, C_EMPTY = 3, C_NEWGAS = 4, C_LIQ2IF = 5, C_FP64 = 6, C_SEG = 7, C_SLOW = 8,
-       C_MLP = 9, C_MLPKEEP = 10, C_ADJ64 = 11, C_NCOUNT = 16 };
+       C_MLP = 9, C_MLPKEEP = 10, C_ADJ64 = 11, C_SEGD0 = 12, C_SEGD1 = 13, C_NCOUNT = 16 };
 
 // the grid is walked in x-row segments of SEG cells (one warp each); a
 // segment is active while it holds a liquid or interface cell
@@ -69,6 +71,7 @@ struct Dev {
     int *iflist;       // interface cells at t
     int *iflist_next;  // interface cells at t+1 (built by the step)
     int cif, cif_next; // their counters
+    int cdirty, cdirty_next;  // segment-set-changed flags of this step and the next
     int *fill, *empty, *newgas, *liq2if;
     int *slow;         // interface cells whose LSQR fit takes the general path
     uint8_t *seg_active;

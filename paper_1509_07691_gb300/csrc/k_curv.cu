@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(LIST_THREADS) k_normals(Dev d) {
     block_counts<1>(d.counts, {d.cif}, cnt);
     const int n = cnt[0];
     if (blockIdx.x == 0 && threadIdx.x == 8) d.counts[d.cif_next] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 9) d.counts[d.cdirty_next] = 0;
     if (blockIdx.x == 0 && threadIdx.x < 8) {
         const int zero[8] = {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF, C_SLOW, C_FP64, C_MLP, C_MLPKEEP};
         d.counts[zero[threadIdx.x]] = 0;
@@ -60,7 +61,20 @@ __global__ void __launch_bounds__(LIST_THREADS) k_normals(Dev d) {
 // when a contact-line cell is present, when there are fewer than five rows,
 // or when the Cholesky pivots estimate cond(A^T A) above d.fp64_cond.
 __device__ bool lsqr_fast(const Dev &d, int i, int x, int y, int z, float &kap) {
-    const float4 c4 = d.normal[i];
+    // flags and stored normals of the whole 3x3x3 block, loaded before any is
+    // used (one round of independent loads)
+    const int xs[3] = {x == 0 ? d.nx - 1 : x - 1, x, x == d.nx - 1 ? 0 : x + 1};
+    const int ys[3] = {y == 0 ? d.ny - 1 : y - 1, y, y == d.ny - 1 ? 0 : y + 1};
+    const int zs[3] = {z == 0 ? d.nz - 1 : z - 1, z, z == d.nz - 1 ? 0 : z + 1};
+    uint8_t fjs[27];
+    float4 q4s[27];
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+        const int jj = cell_index(d, xs[t % 3], ys[(t / 3) % 3], zs[t / 9]);
+        fjs[t] = d.flags[jj];
+        q4s[t] = d.normal[jj];
+    }
+    const float4 c4 = q4s[13];
     kap = 0.f;
     if (c4.x == 0.f && c4.y == 0.f && c4.z == 0.f) return true;
     const float n[3] = {c4.x, c4.y, c4.z};
@@ -83,40 +97,25 @@ __device__ bool lsqr_fast(const Dev &d, int i, int x, int y, int z, float &kap) 
 #pragma unroll
     for (int t = 0; t < 5; ++t) r[t] = 0.f;
     int m = 0;
-    bool contact = (d.flags[i] & B_NEAR) != 0;
-    const int xs[3] = {x == 0 ? d.nx - 1 : x - 1, x, x == d.nx - 1 ? 0 : x + 1};
-    const int ys[3] = {y == 0 ? d.ny - 1 : y - 1, y, y == d.ny - 1 ? 0 : y + 1};
-#pragma unroll 1
-    for (int pz = 0; pz < 3; ++pz) {
-        const int zz = z + pz - 1 < 0 ? d.nz - 1 : (z + pz - 1 >= d.nz ? 0 : z + pz - 1);
-        int jj[9];
-        uint8_t fjs[9];
-        float4 q4s[9];
+    bool contact = (fjs[13] & B_NEAR) != 0;
 #pragma unroll
-        for (int t = 0; t < 9; ++t) jj[t] = cell_index(d, xs[t % 3], ys[t / 3], zz);
+    for (int t = 0; t < 27; ++t) {
+        const float4 q4 = q4s[t];
+        const bool use = (fjs[t] & T_IF) && t != 13 && !(q4.x == 0.f && q4.y == 0.f && q4.z == 0.f);
+        contact |= (fjs[t] & T_IF) && (fjs[t] & B_NEAR);
+        const float w = use ? 1.f : 0.f;
+        const float dv[3] = {(float)(t % 3 - 1) + q4.w * q4.x - p[0], (float)((t / 3) % 3 - 1) + q4.w * q4.y - p[1],
+                             (float)(t / 9 - 1) + q4.w * q4.z - p[2]};
+        const float u = dot3(dv, tu), v = dot3(dv, tv), f = w * dot3(dv, n);
+        const float a[5] = {w * u * u, w * v * v, w * u * v, w * u, w * v};
+        int c = 0;
 #pragma unroll
-        for (int t = 0; t < 9; ++t) fjs[t] = d.flags[jj[t]];
+        for (int a0 = 0; a0 < 5; ++a0) {
 #pragma unroll
-        for (int t = 0; t < 9; ++t) q4s[t] = d.normal[jj[t]];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const float4 q4 = q4s[t];
-            const bool use = (fjs[t] & T_IF) && !(pz == 1 && t == 4) && !(q4.x == 0.f && q4.y == 0.f && q4.z == 0.f);
-            contact |= (fjs[t] & T_IF) && (fjs[t] & B_NEAR);
-            const float w = use ? 1.f : 0.f;
-            const float dv[3] = {(float)(t % 3 - 1) + q4.w * q4.x - p[0], (float)(t / 3 - 1) + q4.w * q4.y - p[1],
-                                 (float)(pz - 1) + q4.w * q4.z - p[2]};
-            const float u = dot3(dv, tu), v = dot3(dv, tv), f = w * dot3(dv, n);
-            const float a[5] = {w * u * u, w * v * v, w * u * v, w * u, w * v};
-            int c = 0;
-#pragma unroll
-            for (int a0 = 0; a0 < 5; ++a0) {
-#pragma unroll
-                for (int a1 = a0; a1 < 5; ++a1) G[c++] += a[a0] * a[a1];
-                r[a0] += a[a0] * f;
-            }
-            m += use ? 1 : 0;
+            for (int a1 = a0; a1 < 5; ++a1) G[c++] += a[a0] * a[a1];
+            r[a0] += a[a0] * f;
         }
+        m += use ? 1 : 0;
     }
     // Cholesky G = R^T R (R upper, packed like G)
     float R[15];

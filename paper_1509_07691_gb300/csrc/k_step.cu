@@ -105,7 +105,10 @@ __global__ void __launch_bounds__(256) k_sc_bulk(Dev d) {
 #pragma unroll
             for (int q = 0; q < Q; ++q) St::st(d.fdst, (long long)q * N + i, q, f[q], d);
         }
-        if (!__any_sync(0xffffffffu, (fl & (T_LIQ | T_IF)) != 0) && lane == 0) d.seg_active[s] = 0;
+        if (!__any_sync(0xffffffffu, (fl & (T_LIQ | T_IF)) != 0) && lane == 0) {
+            d.seg_active[s] = 0;
+            d.counts[d.cdirty] = 1;
+        }
     }
 }
 
@@ -150,6 +153,16 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_sc_iface(Dev d) {
                 wz -= cz(q);
             }
         }
+        // the PDF and fill level of every source cell, loaded unconditionally
+        // (in bounds for every cell type; used only on fluid links) so that
+        // all of a cell's loads are in flight together
+        float fin[Q], phn[Q];
+        fin[0] = phn[0] = 0.f;
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            fin[q] = St::ld(d.fsrc, (long long)q * N + src[q], q, d);
+            phn[q] = d.phi[src[q]];
+        }
         // u_b: velocity of x at time t from its own post-collision PDFs
         float r0 = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
@@ -184,17 +197,12 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_sc_iface(Dev d) {
             const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
             // feq_q + feq_qbar at (rho_b, u_b): the odd terms cancel
             const float recon = 2.0f * wq(q) * rho_b * (1.0f + 4.5f * cu * cu - uu) - fo[qb];
-            if (tq[q] & (T_LIQ | T_IF)) {
-                const float fin = St::ld(d.fsrc, (long long)q * N + src[q], q, d);
-                f[q] = fin;
-                const float kq = (tq[q] & T_LIQ) ? 1.0f : 0.5f * (phix + d.phi[src[q]]);
-                dm += kq * (fin - fo[qb]);
-            } else if (tq[q] & T_OBS) {
-                const float outdir = -(cx(q) * ntx + cy(q) * nty + cz(q) * ntz);  // c_qbar . n_t
-                f[q] = (corner && outdir < 0.f) ? recon : fo[qb];
-            } else {
-                f[q] = recon;
-            }
+            const bool fluid = (tq[q] & (T_LIQ | T_IF)) != 0;
+            const float kq = (tq[q] & T_LIQ) ? 1.0f : 0.5f * (phix + phn[q]);
+            const float outdir = -(cx(q) * ntx + cy(q) * nty + cz(q) * ntz);  // c_qbar . n_t
+            const float bound = ((tq[q] & T_OBS) && !(corner && outdir < 0.f)) ? fo[qb] : recon;
+            f[q] = fluid ? fin[q] : bound;
+            dm += fluid ? kq * (fin[q] - fo[qb]) : 0.f;
         }
         float rho;
         collide<COLL>(f, d, rho);
@@ -264,7 +272,11 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
                 if (!((old >> sh) & B_NEW)) {
                     if (isfill) {
                         d.newgas[atomicAdd(d.counts + C_NEWGAS, 1)] = j;
-                        d.seg_active[seg_of(d, j)] = 1;
+                        const int sj = seg_of(d, j);
+                        if (!d.seg_active[sj]) {
+                            d.seg_active[sj] = 1;
+                            d.counts[d.cdirty] = 1;
+                        }
                     } else {
                         d.liq2if[atomicAdd(d.counts + C_LIQ2IF, 1)] = j;
                     }
@@ -358,9 +370,9 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
 //    and the new ones) gather the excess mass of converted neighbours in fixed
 //    q order, set phi = m / rho and form the interface list of t+1.
 __global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
-    int cnt[5];
-    block_counts<5>(d.counts, {d.cif, C_NEWGAS, C_LIQ2IF, C_FILL, C_EMPTY}, cnt);
-    if (blockIdx.x == 0 && threadIdx.x == 0) d.counts[C_SEG] = 0;  // filled again by k_fin_b
+    int cnt[6];
+    block_counts<6>(d.counts, {d.cif, C_NEWGAS, C_LIQ2IF, C_FILL, C_EMPTY, d.cdirty}, cnt);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cnt[5]) d.counts[C_SEG] = 0;  // filled again by k_fin_b
     const int nold = cnt[0], ngas = cnt[1], nliq = cnt[2];
     const bool any = (cnt[3] + cnt[4]) > 0;
     warp_uniform_loop(nold + ngas + nliq, [&](int k, bool valid) {
@@ -389,10 +401,11 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
 }
 
 // B: final types of the converted cells (transient bits cleared), and the
-// list of active segments for the next step (warp-ballot compaction)
+// list of active segments for the next step (block-aggregated compaction),
+// rebuilt only when a segment was switched on or off during the step
 __global__ void __launch_bounds__(256) k_fin_b(Dev d) {
-    int cnt[4];
-    block_counts<4>(d.counts, {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF}, cnt);
+    int cnt[5];
+    block_counts<5>(d.counts, {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF, d.cdirty}, cnt);
     const int nfill = cnt[0], nempty = cnt[1], ngas = cnt[2], nliq = cnt[3];
     const int n = nfill + nempty + ngas + nliq;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
@@ -414,6 +427,7 @@ __global__ void __launch_bounds__(256) k_fin_b(Dev d) {
             d.flags[j] = T_IF | (d.flags[j] & B_NEAR);
         }
     }
+    if (!cnt[4]) return;  // the set of active segments did not change (block-uniform)
     for (int base = blockIdx.x * blockDim.x; base < d.nseg; base += nth) {
         const int s = base + threadIdx.x;
         block_append(d.seg_list, d.counts + C_SEG, s < d.nseg && d.seg_active[s], s);
