@@ -263,13 +263,19 @@ def run_reference(args):
 PHASES = ["normals_plic", "lsqr_curvature", "sc_liquid", "sc_interface", "convert", "finalize"]
 
 
-def algorithmic_bytes(n_fluid, n_if, n_seg_cells):
-    """Bytes each phase must move at least, per launch (roofline table)."""
-    return {"normals_plic": 21.0 * n_if,           # phi + flag read, normal + offset written
-            "lsqr_curvature": 21.0 * n_if,         # normal + flag read, kappa written
-            "sc_liquid": 152.0 * (n_fluid - n_if) + 1.0 * n_seg_cells,  # 19 PDFs in + 19 out, flags
-            "sc_interface": 248.0 * n_if,          # own + pulled + written PDFs, m, phi, kappa, rho
-            "convert": 0.0, "finalize": 14.0 * n_if}
+def algorithmic_bytes(n_fluid, n_if, n_seg_cells, fused=False):
+    """Bytes each phase must move at least, per launch (roofline table).
+    fused: the LSQR curvature and the interface stream-collide run as one pass
+    (phase lsqr_curvature), the sc_interface phase is empty."""
+    nb = {"normals_plic": 21.0 * n_if,           # phi + flag read, normal + offset written
+          "lsqr_curvature": 21.0 * n_if,         # normal + flag read, kappa written
+          "sc_liquid": 152.0 * (n_fluid - n_if) + 1.0 * n_seg_cells,  # 19 PDFs in + 19 out, flags
+          "sc_interface": 248.0 * n_if,          # own + pulled + written PDFs, m, phi, kappa, rho
+          "convert": 0.0, "finalize": 14.0 * n_if}
+    if fused:
+        nb["lsqr_curvature"] += nb["sc_interface"]
+        nb["sc_interface"] = 0.0
+    return nb
 
 
 def time_steps(sim, steps, stream, flush):
@@ -310,12 +316,13 @@ def measured_traffic(kernel, workload):
     return None
 
 
-def roofline_of(ph, nbytes, peaks, which=None, workload=None):
+def roofline_of(ph, nbytes, peaks, which=None, workload=None, fused=False):
     k = which if which is not None else int(np.argmax(ph))
     name = PHASES[k]
+    label = "lsqr_curvature+sc_interface (fused)" if fused and name == "lsqr_curvature" else name
     hbm = peaks.get("hbm_gbs", 6800.0)
     ach = nbytes[name] / (ph[k] * 1e-3) / 1e9
-    return {"kernel": name, "bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": hbm, "frac": ach / hbm,
+    return {"kernel": label, "bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": hbm, "frac": ach / hbm,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst; of measured)" if peaks else "fallback 6.8 TB/s",
             "traffic": measured_traffic(name, workload) if workload else None,
             "traffic_source": "profiles/ncu_traffic.json (ncu dram bytes per launch)",
@@ -336,7 +343,7 @@ def side_workload(F, S, name, storage, steps, stream, flush, peaks, seed):
     m1, l1 = sim.mass_total()
     ph = phase_profile(sim, min(steps, 20), flush)
     nseg_cells = n_fluid  # liquid rows are dense in this workload
-    nb = algorithmic_bytes(n_fluid, n_if, nseg_cells)
+    nb = algorithmic_bytes(n_fluid, n_if, nseg_cells, fused=True)
     if storage != "f32":
         nb["sc_liquid"] = 76.0 * (n_fluid - n_if) + 1.0 * nseg_cells
     out = {"workload": name, "storage": storage, "fluid_cells": n_fluid, "interface_cells": n_if,
@@ -658,8 +665,9 @@ def run_fsl(args):
            "includes": "fsl_init from pinned host fill levels (upload, types, f = w_q), graph capture, K steps, "
                        "fsl_mass read back"}
 
-    nb = algorithmic_bytes(n_fluid, n_if, n_fluid)
-    roof = roofline_of(ph, nb, peaks, workload=args.workload if args.storage == "f32" else None)
+    fused = args.curv == "lsqr"
+    nb = algorithmic_bytes(n_fluid, n_if, n_fluid, fused=fused)
+    roof = roofline_of(ph, nb, peaks, workload=args.workload if args.storage == "f32" else None, fused=fused)
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"f32": "f32", "f16": "f16-offset/f32", "bf16": "bf16-offset/f32"}[args.storage],
@@ -673,7 +681,7 @@ def run_fsl(args):
             "lsqr_fp64_cells": n_fp64,
             "phases_ms": dict(zip(PHASES, [round(float(v), 5) for v in ph])),
             "mass_reduce_ms": mass_ms, "mass_drift_rel": drift, "roofline": roof, "e2e": e2e,
-            "gpu_launches": 8 * args.steps, "clocks": clocks}
+            "gpu_launches": {"lsqr": 7, "fd": 7, "none": 7}[args.curv] * args.steps, "clocks": clocks}
     gs = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         gs = {"flags": sim2.flags_current().cpu().numpy(), "phi": sim2.phi.double().cpu().numpy()}

@@ -178,8 +178,10 @@ int fsl_stats(struct fsl_ctx *ctx, int64_t counts_out[10]);
 /* One time step like fsl_step(ctx, 1), launched kernel by kernel (no graph,
  * phases in sequence) with CUDA events on the context's stream between its
  * phases; ms_out[0..5] receive the device time of: normals + PLIC, curvature,
- * liquid stream-collide, interface stream-collide, conversion, finalize.
- * For profiling.  Synchronising. */
+ * liquid stream-collide, interface stream-collide, conversion, finalize.  With
+ * the LSQR model the curvature and the interface stream-collide run fused (one
+ * pass per cell): their time is in ms_out[1] and ms_out[3] is the empty
+ * interval.  For profiling.  Synchronising. */
 int fsl_step_profile(struct fsl_ctx *ctx, float ms_out[6]);
 
 /* Total mass of a state (sum of m over interface cells plus sum of rho over

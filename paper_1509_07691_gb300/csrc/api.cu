@@ -183,8 +183,13 @@ int enqueue_step_graph(const fsl_ctx *c, int parity) {
     CK(cudaStreamWaitEvent(side, c->fork, 0));
     launch_sc_bulk(d, side);
     CK(cudaEventRecord(c->join, side));
-    enqueue_curvature(d, c->p.curv_model, d.kappa, s);
-    launch_sc_iface(d, s);
+    if (c->p.curv_model == FSL_CURV_LSQR) {
+        launch_normals(d, s);
+        launch_curv_iface(d, s);
+    } else {
+        enqueue_curvature(d, c->p.curv_model, d.kappa, s);
+        launch_sc_iface(d, s);
+    }
     CK(cudaStreamWaitEvent(s, c->join, 0));
     launch_convert(d, s);
     launch_finalize(d, s);
@@ -431,14 +436,16 @@ int fsl_step_profile(fsl_ctx *c, float ms_out[6]) {
         if (cudaEventRecord(ev[0], s) != cudaSuccess) break;
         launch_normals(d, s);
         if (cudaEventRecord(ev[1], s) != cudaSuccess) break;
-        if (c->p.curv_model == FSL_CURV_LSQR || c->p.curv_model == FSL_CURV_MLP) launch_lsqr(d, d.kappa, s);
+        const bool fused = c->p.curv_model == FSL_CURV_LSQR;
+        if (fused) launch_curv_iface(d, s);  // curvature + interface stream-collide
+        else if (c->p.curv_model == FSL_CURV_MLP) launch_lsqr(d, d.kappa, s);
         else if (c->p.curv_model == FSL_CURV_FD) launch_fd(d, d.kappa, s);
         else launch_zero_kappa(d, d.kappa, s);
         if (c->p.curv_model == FSL_CURV_MLP) launch_mlp_curv(d, d.kappa, s);
         if (cudaEventRecord(ev[2], s) != cudaSuccess) break;
         launch_sc_bulk(d, s);
         if (cudaEventRecord(ev[3], s) != cudaSuccess) break;
-        launch_sc_iface(d, s);
+        if (!fused) launch_sc_iface(d, s);
         if (cudaEventRecord(ev[4], s) != cudaSuccess) break;
         launch_convert(d, s);
         if (cudaEventRecord(ev[5], s) != cudaSuccess) break;

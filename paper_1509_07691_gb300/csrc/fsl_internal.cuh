@@ -232,6 +232,8 @@ void launch_mass(const Dev &d, double *out, cudaStream_t s);
 void launch_stream_collide(const Dev &d, cudaStream_t s);
 void launch_sc_bulk(const Dev &d, cudaStream_t s);
 void launch_sc_iface(const Dev &d, cudaStream_t s);
+// LSQR curvature and interface stream-collide in one pass (after launch_normals)
+void launch_curv_iface(const Dev &d, cudaStream_t s);
 void launch_convert(const Dev &d, cudaStream_t s);
 void launch_finalize(const Dev &d, cudaStream_t s);
 void launch_normals(const Dev &d, cudaStream_t s);

@@ -151,10 +151,13 @@ void launch_window_finish(const Dev &dst, const int *wcounts, const int *wlist, 
 
 void launch_frozen_step(const Dev &d, cudaStream_t s) {
     launch_normals(d, s);
-    if (d.curv_model == FSL_CURV_LSQR) launch_lsqr(d, d.kappa, s);
-    else launch_zero_kappa(d, d.kappa, s);
     launch_sc_bulk(d, s);
-    launch_sc_iface(d, s);
+    if (d.curv_model == FSL_CURV_LSQR) {
+        launch_curv_iface(d, s);
+    } else {
+        launch_zero_kappa(d, d.kappa, s);
+        launch_sc_iface(d, s);
+    }
     launch_fin_frozen(d, s);
 }
 

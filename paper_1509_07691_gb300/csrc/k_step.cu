@@ -7,7 +7,7 @@
 // x-row segments (coalesced SoA loads, one thread per cell); interface cells
 // by k_sc_iface over the interface list; everything after the collision only
 // touches list entries, so no pass sweeps the whole grid.
-#include "fsl_internal.cuh"
+#include "curv_common.cuh"
 
 namespace fslk {
 
@@ -121,104 +121,161 @@ __global__ void __launch_bounds__(256) k_sc_bulk(Dev d) {
 //             contact-line cell when c_qbar . n_t < 0, n_t the interface normal
 //             projected into the wall (Fig. inhomo)
 // plus the mass exchange of Eqs. (advection1/2) and the conversion test
-// (skipped when the types are frozen).
+// (skipped when the types are frozen).  iface_cell reads kappa(x) and, at
+// contact-line cells, the PLIC normal of x -- both the cell's own -- so it may
+// run right after the curvature of the same cell, in the same kernel.
+template <int S, int COLL>
+__device__ __forceinline__ void iface_cell(const Dev &d, int i) {
+    using St = Store<S>;
+    const long long N = d.N;
+    int x, y, z;
+    cell_coords(d, i, x, y, z);
+    int src[Q];
+    sources(d, x, y, z, src);
+    const uint8_t fl = d.flags[i];
+    float fo[Q], f[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) fo[q] = St::ld(d.fsrc, (long long)q * N + i, q, d);
+    uint8_t tq[Q];
+    bool has_gas = false, has_obs = false;
+    float wx = 0.f, wy = 0.f, wz = 0.f;  // sum of vectors x -> obstacle neighbour
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        tq[q] = d.flags[src[q]] & T_MASK;
+        has_gas |= (tq[q] & T_GAS) != 0;
+        if (tq[q] & T_OBS) {
+            has_obs = true;
+            wx -= cx(q);
+            wy -= cy(q);
+            wz -= cz(q);
+        }
+    }
+    // the PDF and fill level of every source cell, loaded unconditionally
+    // (in bounds for every cell type; used only on fluid links) so that
+    // all of a cell's loads are in flight together
+    float fin[Q], phn[Q];
+    fin[0] = phn[0] = 0.f;
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        fin[q] = St::ld(d.fsrc, (long long)q * N + src[q], q, d);
+        phn[q] = d.phi[src[q]];
+    }
+    // u_b: velocity of x at time t from its own post-collision PDFs
+    float r0 = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        r0 += fo[q];
+        jx += cx(q) * fo[q];
+        jy += cy(q) * fo[q];
+        jz += cz(q) * fo[q];
+    }
+    const float ux = jx / r0, uy = jy / r0, uz = jz / r0;
+    const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float rho_b = d.rho_gas + d.six_sigma * d.kappa[i];
+    const bool corner = has_gas && has_obs;
+    float ntx = 0.f, nty = 0.f, ntz = 0.f;
+    if (corner) {
+        const float4 n4 = d.normal[i];
+        const float wl = rsqrtf(wx * wx + wy * wy + wz * wz);
+        wx *= wl;
+        wy *= wl;
+        wz *= wl;
+        const float wn = n4.x * wx + n4.y * wy + n4.z * wz;
+        ntx = n4.x - wn * wx;
+        nty = n4.y - wn * wy;
+        ntz = n4.z - wn * wz;
+    }
+    const float phix = d.phi[i];
+    float dm = 0.f;
+    f[0] = fo[0];
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const int qb = opp(q);
+        const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+        // feq_q + feq_qbar at (rho_b, u_b): the odd terms cancel
+        const float recon = 2.0f * wq(q) * rho_b * (1.0f + 4.5f * cu * cu - uu) - fo[qb];
+        const bool fluid = (tq[q] & (T_LIQ | T_IF)) != 0;
+        const float kq = (tq[q] & T_LIQ) ? 1.0f : 0.5f * (phix + phn[q]);
+        const float outdir = -(cx(q) * ntx + cy(q) * nty + cz(q) * ntz);  // c_qbar . n_t
+        const float bound = ((tq[q] & T_OBS) && !(corner && outdir < 0.f)) ? fo[qb] : recon;
+        f[q] = fluid ? fin[q] : bound;
+        dm += fluid ? kq * (fin[q] - fo[qb]) : 0.f;
+    }
+    float rho;
+    collide<COLL>(f, d, rho);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) St::st(d.fdst, (long long)q * N + i, q, f[q], d);
+    const float m = d.mass[i] + dm;
+    d.mass[i] = m;
+    d.rho[i] = rho;
+    if (d.frozen) return;
+    if (m > (1.0f + d.eps) * rho) {
+        d.flags[i] = fl | B_TOLIQ;
+        d.fill[atomicAdd(d.counts + C_FILL, 1)] = i;
+    } else if (m < -d.eps * rho) {
+        d.flags[i] = fl | B_TOGAS;
+        d.empty[atomicAdd(d.counts + C_EMPTY, 1)] = i;
+    }
+}
+
 template <int S, int COLL>
 __global__ void __launch_bounds__(LIST_BLOCK) k_sc_iface(Dev d) {
-    using St = Store<S>;
     int cnt[1];
     block_counts<1>(d.counts, {d.cif}, cnt);
     const int n = cnt[0];
-    const long long N = d.N;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        iface_cell<S, COLL>(d, d.iflist[k]);
+}
+
+// ---- LSQR curvature fused with the interface stream-collide ----------------------
+// With the LSQR model the curvature of a cell and its stream-collide run in
+// one thread: k_curv_iface_fast fits the cell by the FP32 normal equations
+// (as k_lsqr_fast) and, unless the fit defers the cell to the general path,
+// goes straight on with iface_cell; k_curv_iface_slow finishes the deferred
+// cells (Givens fit, FP64 re-solve when ill conditioned, then iface_cell).
+// iface_cell of one cell changes only that cell's transient flag bits, mass,
+// rho and new PDFs, none of which a fit of another cell reads.
+template <int S, int COLL>
+__global__ void __launch_bounds__(LIST_BLOCK) k_curv_iface_fast(Dev d) {
+    int cnt[1];
+    block_counts<1>(d.counts, {d.cif}, cnt);
+    const int n = cnt[0];
+    warp_uniform_loop(n, [&](int k, bool valid) {
+        bool defer = false;
+        int i = 0;
+        if (valid) {
+            i = d.iflist[k];
+            int x, y, z;
+            cell_coords(d, i, x, y, z);
+            float kap;
+            if (lsqr_fast(d, i, x, y, z, kap)) d.kappa[i] = kap;
+            else defer = true;
+        }
+        warp_append(d.slow, d.counts + C_SLOW, defer, i);
+        if (valid && !defer) iface_cell<S, COLL>(d, i);
+    });
+}
+
+template <int S, int COLL>
+__global__ void __launch_bounds__(LIST_BLOCK) k_curv_iface_slow(Dev d) {
+    int cnt[1];
+    block_counts<1>(d.counts, {C_SLOW}, cnt);
+    const int n = cnt[0];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int i = d.iflist[k];
+        const int i = d.slow[k];
         int x, y, z;
         cell_coords(d, i, x, y, z);
-        int src[Q];
-        sources(d, x, y, z, src);
-        const uint8_t fl = d.flags[i];
-        float fo[Q], f[Q];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) fo[q] = St::ld(d.fsrc, (long long)q * N + i, q, d);
-        uint8_t tq[Q];
-        bool has_gas = false, has_obs = false;
-        float wx = 0.f, wy = 0.f, wz = 0.f;  // sum of vectors x -> obstacle neighbour
-#pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            tq[q] = d.flags[src[q]] & T_MASK;
-            has_gas |= (tq[q] & T_GAS) != 0;
-            if (tq[q] & T_OBS) {
-                has_obs = true;
-                wx -= cx(q);
-                wy -= cy(q);
-                wz -= cz(q);
-            }
+        const GridAcc acc{d, x, y, z};
+        const uint8_t fi = d.flags[i] & (T_MASK | B_NEAR);
+        float cond;
+        float kap = lsqr_core<float>(acc, fi, cond);
+        if (cond * cond > d.fp64_cond) {
+            double c2;
+            kap = (float)lsqr_core<double>(acc, fi, c2);
+            atomicAdd(d.counts + C_FP64, 1);
         }
-        // the PDF and fill level of every source cell, loaded unconditionally
-        // (in bounds for every cell type; used only on fluid links) so that
-        // all of a cell's loads are in flight together
-        float fin[Q], phn[Q];
-        fin[0] = phn[0] = 0.f;
-#pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            fin[q] = St::ld(d.fsrc, (long long)q * N + src[q], q, d);
-            phn[q] = d.phi[src[q]];
-        }
-        // u_b: velocity of x at time t from its own post-collision PDFs
-        float r0 = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            r0 += fo[q];
-            jx += cx(q) * fo[q];
-            jy += cy(q) * fo[q];
-            jz += cz(q) * fo[q];
-        }
-        const float ux = jx / r0, uy = jy / r0, uz = jz / r0;
-        const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
-        const float rho_b = d.rho_gas + d.six_sigma * d.kappa[i];
-        const bool corner = has_gas && has_obs;
-        float ntx = 0.f, nty = 0.f, ntz = 0.f;
-        if (corner) {
-            const float4 n4 = d.normal[i];
-            const float wl = rsqrtf(wx * wx + wy * wy + wz * wz);
-            wx *= wl;
-            wy *= wl;
-            wz *= wl;
-            const float wn = n4.x * wx + n4.y * wy + n4.z * wz;
-            ntx = n4.x - wn * wx;
-            nty = n4.y - wn * wy;
-            ntz = n4.z - wn * wz;
-        }
-        const float phix = d.phi[i];
-        float dm = 0.f;
-        f[0] = fo[0];
-#pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            const int qb = opp(q);
-            const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-            // feq_q + feq_qbar at (rho_b, u_b): the odd terms cancel
-            const float recon = 2.0f * wq(q) * rho_b * (1.0f + 4.5f * cu * cu - uu) - fo[qb];
-            const bool fluid = (tq[q] & (T_LIQ | T_IF)) != 0;
-            const float kq = (tq[q] & T_LIQ) ? 1.0f : 0.5f * (phix + phn[q]);
-            const float outdir = -(cx(q) * ntx + cy(q) * nty + cz(q) * ntz);  // c_qbar . n_t
-            const float bound = ((tq[q] & T_OBS) && !(corner && outdir < 0.f)) ? fo[qb] : recon;
-            f[q] = fluid ? fin[q] : bound;
-            dm += fluid ? kq * (fin[q] - fo[qb]) : 0.f;
-        }
-        float rho;
-        collide<COLL>(f, d, rho);
-#pragma unroll
-        for (int q = 0; q < Q; ++q) St::st(d.fdst, (long long)q * N + i, q, f[q], d);
-        const float m = d.mass[i] + dm;
-        d.mass[i] = m;
-        d.rho[i] = rho;
-        if (d.frozen) continue;
-        if (m > (1.0f + d.eps) * rho) {
-            d.flags[i] = fl | B_TOLIQ;
-            d.fill[atomicAdd(d.counts + C_FILL, 1)] = i;
-        } else if (m < -d.eps * rho) {
-            d.flags[i] = fl | B_TOGAS;
-            d.empty[atomicAdd(d.counts + C_EMPTY, 1)] = i;
-        }
+        d.kappa[i] = kap;
+        iface_cell<S, COLL>(d, i);
     }
 }
 
@@ -485,7 +542,16 @@ void launch_iface(const Dev &d, cudaStream_t s) {
         }                                                                                         \
     } while (0)
 
+template <int S, int COLL>
+void launch_ci(const Dev &d, cudaStream_t s) {
+    static const int gf = list_blocks((const void *)k_curv_iface_fast<S, COLL>, LIST_BLOCK, 4);
+    static const int gs = list_blocks((const void *)k_curv_iface_slow<S, COLL>, LIST_BLOCK, 1);
+    k_curv_iface_fast<S, COLL><<<gf, LIST_BLOCK, 0, s>>>(d);
+    k_curv_iface_slow<S, COLL><<<gs, LIST_BLOCK, 0, s>>>(d);
+}
+
 void launch_sc_bulk(const Dev &d, cudaStream_t s) { FSL_DISPATCH(launch_bulk); }
+void launch_curv_iface(const Dev &d, cudaStream_t s) { FSL_DISPATCH(launch_ci); }
 void launch_sc_iface(const Dev &d, cudaStream_t s) { FSL_DISPATCH(launch_iface); }
 #undef FSL_DISPATCH
 
