@@ -17,14 +17,20 @@ namespace fslk {
 constexpr int LIST_THREADS = 128;
 
 // fill level at any cell (periodic wrap); obstacle cells take the reflection
+// reflected fill level of the obstacle cell (x, y, z); kept out of line: the
+// callers unroll over their stencils and obstacle cells are rare
+__device__ __noinline__ float phi_reflected(const Dev &d, int x, int y, int z) {
+    return reflect_value<float>([&](int a, int b, int c) { return d.flags[nbr_index(d, x, y, z, a, b, c)]; },
+                                [&](int a, int b, int c) { return d.phi[nbr_index(d, x, y, z, a, b, c)]; });
+}
+
 __device__ __forceinline__ float phi_ext(const Dev &d, int x, int y, int z) {
     x = wrap(x, d.nx);
     y = wrap(y, d.ny);
     z = wrap(z, d.nz);
     const int i = cell_index(d, x, y, z);
     if (!(d.flags[i] & T_OBS)) return d.phi[i];
-    return reflect_value<float>([&](int a, int b, int c) { return d.flags[nbr_index(d, x, y, z, a, b, c)]; },
-                                [&](int a, int b, int c) { return d.phi[nbr_index(d, x, y, z, a, b, c)]; });
+    return phi_reflected(d, x, y, z);
 }
 
 // The first kernel of a step also zeroes that step's counters (conversion
