@@ -484,66 +484,59 @@ struct GridAcc {
 // Fast path: FP32 normal equations of the full model for an interface cell
 // with no contact-line cell in its neighbourhood.  The 5x5 Gram matrix
 // A^T A and A^T f are accumulated row by row (independent FMAs), then solved
-// by Cholesky in registers.  Returns false (cell left to the general path)
-// when a contact-line cell is present, when there are fewer than five rows,
-// or when the Cholesky pivots estimate cond(A^T A) above d.fp64_cond.
-__device__ __forceinline__ bool lsqr_fast(const Dev &d, int i, int x, int y, int z, float &kap) {
-    // flags and stored normals of the whole 3x3x3 block, loaded before any is
-    // used (one round of independent loads)
-    const int xs[3] = {x == 0 ? d.nx - 1 : x - 1, x, x == d.nx - 1 ? 0 : x + 1};
-    const int ys[3] = {y == 0 ? d.ny - 1 : y - 1, y, y == d.ny - 1 ? 0 : y + 1};
-    const int zs[3] = {z == 0 ? d.nz - 1 : z - 1, z, z == d.nz - 1 ? 0 : z + 1};
-    uint8_t fjs[27];
-    float4 q4s[27];
-#pragma unroll
-    for (int t = 0; t < 27; ++t) {
-        const int jj = cell_index(d, xs[t % 3], ys[(t / 3) % 3], zs[t / 9]);
-        fjs[t] = d.flags[jj];
-        q4s[t] = d.normal[jj];
-    }
-    const float4 c4 = q4s[13];
-    kap = 0.f;
-    if (c4.x == 0.f && c4.y == 0.f && c4.z == 0.f) return true;
-    const float n[3] = {c4.x, c4.y, c4.z};
+// by Cholesky in registers.  The fit is rejected (cell left to the general
+// path) when a contact-line cell is present, when there are fewer than five
+// rows, or when the Cholesky pivots estimate cond(A^T A) above fp64_cond.
+// In three parts so that the rows can be split over several lanes:
+// lsqr_fast_frame, lsqr_fast_row (for each neighbour slot t of the 3x3x3
+// block, t = (dz+1)*9 + (dy+1)*3 + (dx+1), centre 13), lsqr_fast_solve.
+struct FastFrame {
+    float n[3], tu[3], tv[3], p[3];
+};
+
+__device__ __forceinline__ void lsqr_fast_frame(const float4 c4, FastFrame &F) {
+    F.n[0] = c4.x;
+    F.n[1] = c4.y;
+    F.n[2] = c4.z;
     int k = 0;
-    if (fabsf(n[1]) < fabsf(n[0])) k = 1;
-    if (fabsf(n[2]) < fabsf(n[k])) k = 2;
-    float tu[3];
-    if (k == 0) { tu[0] = 0.f; tu[1] = -n[2]; tu[2] = n[1]; }
-    else if (k == 1) { tu[0] = n[2]; tu[1] = 0.f; tu[2] = -n[0]; }
-    else { tu[0] = -n[1]; tu[1] = n[0]; tu[2] = 0.f; }
-    const float tl = rsqrtf(dot3(tu, tu));
-    tu[0] *= tl;
-    tu[1] *= tl;
-    tu[2] *= tl;
-    const float tv[3] = {n[1] * tu[2] - n[2] * tu[1], n[2] * tu[0] - n[0] * tu[2], n[0] * tu[1] - n[1] * tu[0]};
-    const float p[3] = {c4.w * n[0], c4.w * n[1], c4.w * n[2]};
-    float G[15], r[5];
+    if (fabsf(F.n[1]) < fabsf(F.n[0])) k = 1;
+    if (fabsf(F.n[2]) < fabsf(F.n[k])) k = 2;
+    if (k == 0) { F.tu[0] = 0.f; F.tu[1] = -F.n[2]; F.tu[2] = F.n[1]; }
+    else if (k == 1) { F.tu[0] = F.n[2]; F.tu[1] = 0.f; F.tu[2] = -F.n[0]; }
+    else { F.tu[0] = -F.n[1]; F.tu[1] = F.n[0]; F.tu[2] = 0.f; }
+    const float tl = rsqrtf(dot3(F.tu, F.tu));
+    F.tu[0] *= tl;
+    F.tu[1] *= tl;
+    F.tu[2] *= tl;
+    F.tv[0] = F.n[1] * F.tu[2] - F.n[2] * F.tu[1];
+    F.tv[1] = F.n[2] * F.tu[0] - F.n[0] * F.tu[2];
+    F.tv[2] = F.n[0] * F.tu[1] - F.n[1] * F.tu[0];
+    F.p[0] = c4.w * F.n[0];
+    F.p[1] = c4.w * F.n[1];
+    F.p[2] = c4.w * F.n[2];
+}
+
+__device__ __forceinline__ void lsqr_fast_row(int t, uint8_t fj, const float4 q4, const FastFrame &F, float G[15],
+                                              float r[5], int &m, bool &contact) {
+    const bool use = (fj & T_IF) && t != 13 && !(q4.x == 0.f && q4.y == 0.f && q4.z == 0.f);
+    contact |= (fj & T_IF) && (fj & B_NEAR);
+    const float w = use ? 1.f : 0.f;
+    const float dv[3] = {(float)(t % 3 - 1) + q4.w * q4.x - F.p[0], (float)((t / 3) % 3 - 1) + q4.w * q4.y - F.p[1],
+                         (float)(t / 9 - 1) + q4.w * q4.z - F.p[2]};
+    const float u = dot3(dv, F.tu), v = dot3(dv, F.tv), f = w * dot3(dv, F.n);
+    const float a[5] = {w * u * u, w * v * v, w * u * v, w * u, w * v};
+    int c = 0;
 #pragma unroll
-    for (int t = 0; t < 15; ++t) G[t] = 0.f;
+    for (int a0 = 0; a0 < 5; ++a0) {
 #pragma unroll
-    for (int t = 0; t < 5; ++t) r[t] = 0.f;
-    int m = 0;
-    bool contact = (fjs[13] & B_NEAR) != 0;
-#pragma unroll
-    for (int t = 0; t < 27; ++t) {
-        const float4 q4 = q4s[t];
-        const bool use = (fjs[t] & T_IF) && t != 13 && !(q4.x == 0.f && q4.y == 0.f && q4.z == 0.f);
-        contact |= (fjs[t] & T_IF) && (fjs[t] & B_NEAR);
-        const float w = use ? 1.f : 0.f;
-        const float dv[3] = {(float)(t % 3 - 1) + q4.w * q4.x - p[0], (float)((t / 3) % 3 - 1) + q4.w * q4.y - p[1],
-                             (float)(t / 9 - 1) + q4.w * q4.z - p[2]};
-        const float u = dot3(dv, tu), v = dot3(dv, tv), f = w * dot3(dv, n);
-        const float a[5] = {w * u * u, w * v * v, w * u * v, w * u, w * v};
-        int c = 0;
-#pragma unroll
-        for (int a0 = 0; a0 < 5; ++a0) {
-#pragma unroll
-            for (int a1 = a0; a1 < 5; ++a1) G[c++] += a[a0] * a[a1];
-            r[a0] += a[a0] * f;
-        }
-        m += use ? 1 : 0;
+        for (int a1 = a0; a1 < 5; ++a1) G[c++] += a[a0] * a[a1];
+        r[a0] += a[a0] * f;
     }
+    m += use ? 1 : 0;
+}
+
+__device__ __forceinline__ bool lsqr_fast_solve(const float G[15], const float r[5], int m, bool contact,
+                                                float fp64_cond, float &kap) {
     // Cholesky G = R^T R (R upper, packed like G)
     float R[15];
     float dmax = 0.f, dmin = 3.0e38f;
@@ -573,7 +566,7 @@ __device__ __forceinline__ bool lsqr_fast(const Dev &d, int i, int x, int y, int
         }
     }
     const float cond = (dmax / dmin) * (dmax / dmin);
-    const bool ok = !contact && m >= 5 && pd && !(cond > d.fp64_cond);
+    const bool ok = !contact && m >= 5 && pd && !(cond > fp64_cond);
     // R^T y = r, R x = y
     float yv[5], sol[5];
 #pragma unroll
@@ -594,6 +587,37 @@ __device__ __forceinline__ bool lsqr_fast(const Dev &d, int i, int x, int y, int
     const float g = 1.0f + H * H + I * I;
     kap = (A * (1.0f + I * I) + B * (1.0f + H * H) - C * H * I) / (g * sqrtf(g));
     return ok;
+}
+
+// one thread per cell: the flags and stored normals of the whole 3x3x3
+// block are loaded before any is used (one round of independent loads)
+__device__ __forceinline__ bool lsqr_fast(const Dev &d, int i, int x, int y, int z, float &kap) {
+    const int xs[3] = {x == 0 ? d.nx - 1 : x - 1, x, x == d.nx - 1 ? 0 : x + 1};
+    const int ys[3] = {y == 0 ? d.ny - 1 : y - 1, y, y == d.ny - 1 ? 0 : y + 1};
+    const int zs[3] = {z == 0 ? d.nz - 1 : z - 1, z, z == d.nz - 1 ? 0 : z + 1};
+    uint8_t fjs[27];
+    float4 q4s[27];
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+        const int jj = cell_index(d, xs[t % 3], ys[(t / 3) % 3], zs[t / 9]);
+        fjs[t] = d.flags[jj];
+        q4s[t] = d.normal[jj];
+    }
+    const float4 c4 = q4s[13];
+    kap = 0.f;
+    if (c4.x == 0.f && c4.y == 0.f && c4.z == 0.f) return true;
+    FastFrame F;
+    lsqr_fast_frame(c4, F);
+    float G[15], r[5];
+#pragma unroll
+    for (int t = 0; t < 15; ++t) G[t] = 0.f;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) r[t] = 0.f;
+    int m = 0;
+    bool contact = (fjs[13] & B_NEAR) != 0;
+#pragma unroll
+    for (int t = 0; t < 27; ++t) lsqr_fast_row(t, fjs[t], q4s[t], F, G, r, m, contact);
+    return lsqr_fast_solve(G, r, m, contact, d.fp64_cond, kap);
 }
 
 }  // namespace fslk

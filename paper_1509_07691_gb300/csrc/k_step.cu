@@ -229,31 +229,262 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_sc_iface(Dev d) {
 
 // ---- LSQR curvature fused with the interface stream-collide ----------------------
 // With the LSQR model the curvature of a cell and its stream-collide run in
-// one thread: k_curv_iface_fast fits the cell by the FP32 normal equations
+// one pass: k_curv_iface_fast fits the cell by the FP32 normal equations
 // (as k_lsqr_fast) and, unless the fit defers the cell to the general path,
-// goes straight on with iface_cell; k_curv_iface_slow finishes the deferred
-// cells (Givens fit, FP64 re-solve when ill conditioned, then iface_cell).
+// goes straight on with the cell's stream-collide, four lanes per cell;
+// k_curv_iface_slow finishes the deferred cells one thread each (Givens fit,
+// FP64 re-solve when ill conditioned, then iface_cell).
 // iface_cell of one cell changes only that cell's transient flag bits, mass,
 // rho and new PDFs, none of which a fit of another cell reads.
-template <int S, int COLL>
-__global__ void __launch_bounds__(LIST_BLOCK) k_curv_iface_fast(Dev d) {
+// Lattice directions by pair: pair p (0..8) holds q = 2p + 1 with velocity
+// c_p and q + 1 with -c_p.  Components packed two bits per pair (1 -> +1,
+// 3 -> -1) so that a lane can decode its own pairs without a table.
+constexpr unsigned PAIR_CX = 0x1541u;   // p: 0:+1 1:0 2:0 3:+1 4:+1 5:+1 6:+1 7:0 8:0
+constexpr unsigned PAIR_CY = 0x14344u;  // p: 0:0 1:+1 2:0 3:+1 4:-1 5:0 6:0 7:+1 8:+1
+constexpr unsigned PAIR_CZ = 0x37410u;  // p: 0:0 1:0 2:+1 3:0 4:0 5:+1 6:-1 7:+1 8:-1
+__device__ __forceinline__ int pair_c(unsigned packed, int p) {
+    const int v = (packed >> (2 * p)) & 3;
+    return v == 3 ? -1 : v;
+}
+
+// L lanes per interface cell (a group), rank r = lane % L.  The fit's 27
+// block cells are split t = r, r + L, ...; the 9 direction pairs p = r,
+// r + L, ...; the rest population goes to rank L - 1.  Partial sums are
+// combined over the group by xor-shuffles in a fixed order.
+template <int L>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int L>
+__device__ __forceinline__ int group_or(int v) {
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// lanes per cell of the fused fit + stream-collide, and the blocks per SM its
+// register budget is held to (one wave of the list on a 256^3 droplet)
+#ifndef FSL_IFACE_LANES
+#define FSL_IFACE_LANES 2
+#endif
+constexpr int IFACE_MIN_BLOCKS = FSL_IFACE_LANES == 4 ? 3 : 3;
+
+template <int S, int COLL, int L>
+__global__ void __launch_bounds__(LIST_BLOCK, IFACE_MIN_BLOCKS) k_curv_iface_fast(Dev d) {
+    using St = Store<S>;
     int cnt[1];
     block_counts<1>(d.counts, {d.cif}, cnt);
     const int n = cnt[0];
-    warp_uniform_loop(n, [&](int k, bool valid) {
-        bool defer = false;
-        int i = 0;
-        if (valid) {
-            i = d.iflist[k];
-            int x, y, z;
-            cell_coords(d, i, x, y, z);
-            float kap;
-            if (lsqr_fast(d, i, x, y, z, kap)) d.kappa[i] = kap;
-            else defer = true;
+    const long long N = d.N;
+    constexpr int CPW = 32 / L;                 // cells per warp
+    constexpr int RS = (27 + L - 1) / L;        // fit rows per lane
+    constexpr int PJ = (9 + L - 1) / L;         // direction pairs per lane
+    const int lane = threadIdx.x & 31, r = lane % L;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int base = gw * CPW; base < n; base += nwarps * CPW) {  // warp-uniform
+        const int k = base + lane / L;
+        const bool valid = k < n;
+        const int i = d.iflist[valid ? k : base];
+        int x, y, z;
+        cell_coords(d, i, x, y, z);
+        // neighbour coordinates (periodic), picked by select: lane-dependent
+        // indices into small arrays would put the arrays in local memory
+        const int xm = x == 0 ? d.nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? d.ny - 1 : y - 1, yp = y == d.ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? d.nz - 1 : z - 1, zp = z == d.nz - 1 ? 0 : z + 1;
+        auto px = [&](int o) { return o < 0 ? xm : (o > 0 ? xp : x); };
+        auto py = [&](int o) { return o < 0 ? ym : (o > 0 ? yp : y); };
+        auto pz = [&](int o) { return o < 0 ? zm : (o > 0 ? zp : z); };
+        // ---- LSQR fit (FP32 normal equations), rows split over the group
+        const float4 c4 = d.normal[i];
+        uint8_t fjs[RS];
+        float4 q4s[RS];
+#pragma unroll
+        for (int s7 = 0; s7 < RS; ++s7) {
+            const int t = r + L * s7;
+            const int tt = t < 27 ? t : 13;
+            const int jj = cell_index(d, px(tt % 3 - 1), py((tt / 3) % 3 - 1), pz(tt / 9 - 1));
+            fjs[s7] = d.flags[jj];
+            q4s[s7] = d.normal[jj];
         }
-        warp_append(d.slow, d.counts + C_SLOW, defer, i);
-        if (valid && !defer) iface_cell<S, COLL>(d, i);
-    });
+        const uint8_t fl = d.flags[i];
+        const float phix = d.phi[i];
+        // ---- the stream-collide's loads (independent of kappa), issued with the fit's
+        float fo[PJ][2], fin[PJ][2], phn[PJ][2];
+        uint8_t tq[PJ][2];
+        float fo0 = 0.f;
+        float r0 = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, wx = 0.f, wy = 0.f, wz = 0.f;
+        int gas = 0, obs = 0;
+#pragma unroll
+        for (int j = 0; j < PJ; ++j) {
+            const int p = r + L * j;
+            const int pp = p < 9 ? p : 0;
+            const int ex = pair_c(PAIR_CX, pp), ey = pair_c(PAIR_CY, pp), ez = pair_c(PAIR_CZ, pp);
+            const int q = 2 * pp + 1;
+            const int sq = cell_index(d, px(-ex), py(-ey), pz(-ez));  // x - c_q
+            const int sb = cell_index(d, px(ex), py(ey), pz(ez));     // x + c_q
+            fo[j][0] = St::ld(d.fsrc, (long long)q * N + i, q, d);
+            fo[j][1] = St::ld(d.fsrc, (long long)(q + 1) * N + i, q + 1, d);
+            tq[j][0] = d.flags[sq] & T_MASK;
+            tq[j][1] = d.flags[sb] & T_MASK;
+            fin[j][0] = St::ld(d.fsrc, (long long)q * N + sq, q, d);
+            fin[j][1] = St::ld(d.fsrc, (long long)(q + 1) * N + sb, q + 1, d);
+            phn[j][0] = d.phi[sq];
+            phn[j][1] = d.phi[sb];
+        }
+        if (r == L - 1) fo0 = St::ld(d.fsrc, i, 0, d);
+        const bool nozero = !(c4.x == 0.f && c4.y == 0.f && c4.z == 0.f);
+        FastFrame F;
+        lsqr_fast_frame(nozero ? c4 : make_float4(0.f, 0.f, 1.f, 0.f), F);
+        float G[15], rv[5];
+#pragma unroll
+        for (int t = 0; t < 15; ++t) G[t] = 0.f;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) rv[t] = 0.f;
+        int m = 0;
+        bool contact = r == 0 && (fl & B_NEAR) != 0;
+#pragma unroll
+        for (int s7 = 0; s7 < RS; ++s7) {
+            const int t = r + L * s7;
+            if (t < 27) lsqr_fast_row(t, fjs[s7], q4s[s7], F, G, rv, m, contact);
+        }
+#pragma unroll
+        for (int t = 0; t < 15; ++t) G[t] = group_sum<L>(G[t]);
+#pragma unroll
+        for (int t = 0; t < 5; ++t) rv[t] = group_sum<L>(rv[t]);
+#pragma unroll
+        for (int o = 1; o < L; o <<= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+        contact = group_or<L>(contact ? 1 : 0) != 0;
+        float kap = 0.f;
+        const bool ok = nozero ? lsqr_fast_solve(G, rv, m, contact, d.fp64_cond, kap) : true;
+        if (!nozero) kap = 0.f;
+        const bool defer = valid && !ok;
+        const bool act = valid && ok;  // group-uniform
+        // ---- interface stream-collide of the cell, direction pairs over the group
+#pragma unroll
+        for (int j = 0; j < PJ; ++j) {
+            const int p = r + L * j;
+            if (p < 9) {
+                const int ex = pair_c(PAIR_CX, p), ey = pair_c(PAIR_CY, p), ez = pair_c(PAIR_CZ, p);
+                r0 += fo[j][0] + fo[j][1];
+                const float dj = fo[j][0] - fo[j][1];
+                jx += ex * dj;
+                jy += ey * dj;
+                jz += ez * dj;
+                gas |= ((tq[j][0] | tq[j][1]) & T_GAS) ? 1 : 0;
+                if (tq[j][0] & T_OBS) { obs = 1; wx -= ex; wy -= ey; wz -= ez; }
+                if (tq[j][1] & T_OBS) { obs = 1; wx += ex; wy += ey; wz += ez; }
+            }
+        }
+        if (r == L - 1) r0 += fo0;
+        r0 = group_sum<L>(r0);
+        jx = group_sum<L>(jx);
+        jy = group_sum<L>(jy);
+        jz = group_sum<L>(jz);
+        wx = group_sum<L>(wx);
+        wy = group_sum<L>(wy);
+        wz = group_sum<L>(wz);
+        gas = group_or<L>(gas);
+        obs = group_or<L>(obs);
+        const float ux = jx / r0, uy = jy / r0, uz = jz / r0;
+        const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+        const float rho_b = d.rho_gas + d.six_sigma * kap;
+        const bool corner = gas && obs;
+        float ntx = 0.f, nty = 0.f, ntz = 0.f;
+        if (corner) {
+            const float wl = rsqrtf(wx * wx + wy * wy + wz * wz);
+            const float vx = wx * wl, vy = wy * wl, vz = wz * wl;
+            const float wn = c4.x * vx + c4.y * vy + c4.z * vz;
+            ntx = c4.x - wn * vx;
+            nty = c4.y - wn * vy;
+            ntz = c4.z - wn * vz;
+        }
+        float g[PJ][2];
+        float dm = 0.f, rg = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+        for (int j = 0; j < PJ; ++j) {
+            const int p = r + L * j;
+            const int pp = p < 9 ? p : 0;
+            const int ex = pair_c(PAIR_CX, pp), ey = pair_c(PAIR_CY, pp), ez = pair_c(PAIR_CZ, pp);
+            const float w = pp < 3 ? 1.0f / 18.0f : 1.0f / 36.0f;
+            const float cu = ex * ux + ey * uy + ez * uz;
+            const float base2 = 2.0f * w * rho_b * (1.0f + 4.5f * cu * cu - uu);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float sgn = h == 0 ? 1.0f : -1.0f;  // c = sgn c_p
+                const float recon = base2 - fo[j][1 - h];
+                const bool fluid = (tq[j][h] & (T_LIQ | T_IF)) != 0;
+                const float kq = (tq[j][h] & T_LIQ) ? 1.0f : 0.5f * (phix + phn[j][h]);
+                const float outdir = -sgn * (ex * ntx + ey * nty + ez * ntz);  // c_qbar . n_t
+                const float bound = ((tq[j][h] & T_OBS) && !(corner && outdir < 0.f)) ? fo[j][1 - h] : recon;
+                g[j][h] = fluid ? fin[j][h] : bound;
+                dm += (fluid && p < 9) ? kq * (fin[j][h] - fo[j][1 - h]) : 0.f;
+            }
+            if (p < 9) {
+                rg += g[j][0] + g[j][1];
+                const float dg = g[j][0] - g[j][1];
+                gx += ex * dg;
+                gy += ey * dg;
+                gz += ez * dg;
+            }
+        }
+        if (r == L - 1) rg += fo0;
+        rg = group_sum<L>(rg);
+        gx = group_sum<L>(gx);
+        gy = group_sum<L>(gy);
+        gz = group_sum<L>(gz);
+        dm = group_sum<L>(dm);
+        // collision (Eq. lbe2) of the cell's own pairs
+        const float inv = 1.0f / rg;
+        const float vx = gx * inv, vy = gy * inv, vz = gz * inv;
+        const float vv = 1.5f * (vx * vx + vy * vy + vz * vz);
+#pragma unroll
+        for (int j = 0; j < PJ; ++j) {
+            const int p = r + L * j;
+            const int pp = p < 9 ? p : 0;
+            const int ex = pair_c(PAIR_CX, pp), ey = pair_c(PAIR_CY, pp), ez = pair_c(PAIR_CZ, pp);
+            const float w = pp < 3 ? 1.0f / 18.0f : 1.0f / 36.0f;
+            const int q = 2 * pp + 1;
+            const float cu = ex * vx + ey * vy + ez * vz;
+            float a0, a1;
+            if (COLL == FSL_BGK) {
+                const float fe0 = w * rg * (1.0f + 3.0f * cu + 4.5f * cu * cu - vv);
+                const float fe1 = w * rg * (1.0f - 3.0f * cu + 4.5f * cu * cu - vv);
+                a0 = g[j][0] + d.omega_e * (fe0 - g[j][0]);
+                a1 = g[j][1] + d.omega_e * (fe1 - g[j][1]);
+            } else {
+                const float ep = w * rg * (1.0f + 4.5f * cu * cu - vv);
+                const float em = w * rg * 3.0f * cu;
+                const float fp = 0.5f * (g[j][0] + g[j][1]), fm = 0.5f * (g[j][0] - g[j][1]);
+                const float de = d.omega_e * (fp - ep), dd = d.omega_o * (fm - em);
+                a0 = g[j][0] - de - dd;
+                a1 = g[j][1] - de + dd;
+            }
+            if (act && p < 9) {
+                St::st(d.fdst, (long long)q * N + i, q, a0, d);
+                St::st(d.fdst, (long long)(q + 1) * N + i, q + 1, a1, d);
+            }
+        }
+        if (act && r == L - 1) St::st(d.fdst, i, 0, fo0 + d.omega_e * ((1.0f / 3.0f) * rg * (1.0f - vv) - fo0), d);
+        warp_append(d.slow, d.counts + C_SLOW, defer && r == 0, i);
+        if (act && r == 0) {
+            d.kappa[i] = kap;
+            const float mm = d.mass[i] + dm;
+            d.mass[i] = mm;
+            d.rho[i] = rg;
+            if (!d.frozen) {
+                if (mm > (1.0f + d.eps) * rg) {
+                    d.flags[i] = fl | B_TOLIQ;
+                    d.fill[atomicAdd(d.counts + C_FILL, 1)] = i;
+                } else if (mm < -d.eps * rg) {
+                    d.flags[i] = fl | B_TOGAS;
+                    d.empty[atomicAdd(d.counts + C_EMPTY, 1)] = i;
+                }
+            }
+        }
+    }
 }
 
 template <int S, int COLL>
@@ -544,9 +775,9 @@ void launch_iface(const Dev &d, cudaStream_t s) {
 
 template <int S, int COLL>
 void launch_ci(const Dev &d, cudaStream_t s) {
-    static const int gf = list_blocks((const void *)k_curv_iface_fast<S, COLL>, LIST_BLOCK, 4);
+    static const int gf = list_blocks((const void *)k_curv_iface_fast<S, COLL, FSL_IFACE_LANES>, LIST_BLOCK, 4);
     static const int gs = list_blocks((const void *)k_curv_iface_slow<S, COLL>, LIST_BLOCK, 1);
-    k_curv_iface_fast<S, COLL><<<gf, LIST_BLOCK, 0, s>>>(d);
+    k_curv_iface_fast<S, COLL, FSL_IFACE_LANES><<<gf, LIST_BLOCK, 0, s>>>(d);
     k_curv_iface_slow<S, COLL><<<gs, LIST_BLOCK, 0, s>>>(d);
 }
 
