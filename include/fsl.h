@@ -235,8 +235,16 @@ int fsl_mlp_stencils(int n, const float *axes, const float *quat, const float *d
                      void *stream);
 
 /* y [n] = network(X [n][128] bf16); with z1, z2 (each [n][128] floats) the
- * pre-activations are kept for the backward pass.  Asynchronous. */
+ * pre-activations are kept for the backward pass.  Runs on the tcgen05 tensor
+ * cores (both layers as 128 x 128 x 128 BF16 MMAs per 128-row tile, FP32
+ * accumulators in tensor memory); uses about 133 KB of shared memory per SM.
+ * Asynchronous; fsl_mlp_status reports a wait that ran out. */
 int fsl_mlp_forward(const void *params, const void *X, int n, float *y, float *z1, float *z2, void *stream);
+
+/* Sticky status of the tensor-core MLP kernels of this device: FSL_OK, or
+ * FSL_ETIMEOUT if a bounded wait for the tensor cores ran out (the tiles not
+ * finished are left unwritten).  reset != 0 clears it.  Synchronising. */
+int fsl_mlp_status(int reset);
 
 /* Bytes of workspace the training calls need for a batch of n. */
 size_t fsl_mlp_train_workspace(int n);

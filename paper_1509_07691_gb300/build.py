@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libfsl.so")
-SOURCES = ["api.cu", "k_init.cu", "k_step.cu", "k_curv.cu", "k_mlp.cu", "k_mass_static.cu", "k_adj.cu"]
+SOURCES = ["api.cu", "k_init.cu", "k_step.cu", "k_curv.cu", "k_mlp.cu", "k_mass_static.cu", "k_adj.cu", "k_mlp_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-I", INCLUDE,
          "-I", CSRC]

@@ -241,6 +241,10 @@ void launch_lsqr(const Dev &d, float *kappa_out, cudaStream_t s);
 void launch_fd(const Dev &d, float *kappa_out, cudaStream_t s);
 void launch_zero_kappa(const Dev &d, float *kappa_out, cudaStream_t s);
 void launch_mlp_curv(const Dev &d, float *kappa_out, cudaStream_t s);
+// batch forward of the MLP on the tcgen05 tensor cores (k_mlp_tc.cu)
+int launch_mlp_forward_tc(const uint8_t *params, const __nv_bfloat16 *X, int n, float *y, float *z1, float *z2,
+                          cudaStream_t s);
+int mlp_tc_status(bool reset);
 void launch_fin_frozen(const Dev &d, cudaStream_t s);
 
 int max_partials();

@@ -1,8 +1,9 @@
 // k_mlp.cu -- learned curvature on the 5x5x5 fill-level stencil: training
-// stencils, the MLP 125 -> 128 -> 128 -> 1 (GELU) with BF16 weights on the
-// tensor cores (mma.sync m16n8k16, FP32 accumulate), its FP32 backward and
-// Adam, and the in-step estimate that keeps the LSQR fit (Sec. II.C) as judge
-// and fallback.
+// stencils, the MLP 125 -> 128 -> 128 -> 1 (GELU) with BF16 weights, its FP32
+// backward and Adam, and the in-step estimate that keeps the LSQR fit
+// (Sec. II.C) as judge and fallback.  The batch forward (training, checks)
+// runs on the tcgen05 tensor cores (k_mlp_tc.cu); the in-step estimate, which
+// gathers 16 stencils per warp from the grid, on mma.sync m16n8k16 here.
 //
 // Network (packed parameter block, see include/fsl.h):
 //   x = bf16(2 phi - 1) over the canonical stencil (125 values, 3 zero pads)
@@ -144,38 +145,7 @@ __device__ void warp_mlp(const MlpSmem &s, const __nv_bfloat16 *Xw, float &y_lo,
     y_hi = yhi + s.b3;
 }
 
-// ---- forward over a batch of stencils (training and checks) -------------------
-template <bool STORE>
-__global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp_forward(const uint8_t *params, const __nv_bfloat16 *X, int n,
-                                                                 float *y, float *z1, float *z2) {
-    extern __shared__ __align__(16) uint8_t smem_raw[];
-    MlpSmem &s = *reinterpret_cast<MlpSmem *>(smem_raw);
-    __nv_bfloat16 *Xs = reinterpret_cast<__nv_bfloat16 *>(smem_raw + sizeof(MlpSmem));
-    load_weights(s, params);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __nv_bfloat16 *Xw = Xs + warp * 16 * WPAD;
-    __syncthreads();
-    for (long long base = (long long)blockIdx.x * MLP_ROWS; base < n; base += (long long)gridDim.x * MLP_ROWS) {
-        const long long r0 = base + warp * 16;
-        const int nvalid = (int)(n - r0 < 16 ? (n - r0 > 0 ? n - r0 : 0) : 16);
-        // 16 rows x 128 bf16 = 16 x 16 uint4 per warp
-        for (int e = lane; e < 16 * 16; e += 32) {
-            const int r = e >> 4, c = (e & 15) * 8;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (r < nvalid) v = *reinterpret_cast<const uint4 *>(X + (r0 + r) * MK + c);
-            *reinterpret_cast<uint4 *>(Xw + r * WPAD + c) = v;
-        }
-        __syncwarp();
-        float ylo, yhi;
-        warp_mlp<STORE>(s, Xw, ylo, yhi, z1, z2, r0, nvalid);
-        if ((lane & 3) == 0) {
-            const int g = lane >> 2;
-            if (g < nvalid) y[r0 + g] = ylo;
-            if (g + 8 < nvalid) y[r0 + g + 8] = yhi;
-        }
-        __syncwarp();
-    }
-}
+
 
 // ---- backward (FP32): deltas, then weight gradients ------------------------
 // loss = (1/n) sum w (y - t)^2, w = 1/(t^2 + 7e-5)
@@ -591,20 +561,11 @@ int fsl_mlp_stencils(int n, const float *axes, const float *quat, const float *d
 int fsl_mlp_forward(const void *params, const void *X, int n, float *y, float *z1, float *z2, void *stream) {
     if (!params || !X || !y || n < 0 || ((z1 == nullptr) != (z2 == nullptr))) return FSL_EINVAL;
     if (n == 0) return FSL_OK;
-    const size_t sm = mlp_forward_smem();
-    cudaStream_t s = (cudaStream_t)stream;
-    const int blocks_needed = (n + MLP_ROWS - 1) / MLP_ROWS;
-    if (z1) {
-        static const int g = mlp_grid((const void *)k_mlp_forward<true>, 32 * MLP_WARPS, sm);
-        k_mlp_forward<true><<<blocks_needed < g ? blocks_needed : g, 32 * MLP_WARPS, sm, s>>>(
-            static_cast<const uint8_t *>(params), static_cast<const __nv_bfloat16 *>(X), n, y, z1, z2);
-    } else {
-        static const int g = mlp_grid((const void *)k_mlp_forward<false>, 32 * MLP_WARPS, sm);
-        k_mlp_forward<false><<<blocks_needed < g ? blocks_needed : g, 32 * MLP_WARPS, sm, s>>>(
-            static_cast<const uint8_t *>(params), static_cast<const __nv_bfloat16 *>(X), n, y, nullptr, nullptr);
-    }
-    return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
+    return launch_mlp_forward_tc(static_cast<const uint8_t *>(params), static_cast<const __nv_bfloat16 *>(X), n, y, z1,
+                                 z2, (cudaStream_t)stream);
 }
+
+int fsl_mlp_status(int reset) { return mlp_tc_status(reset != 0); }
 
 // forward + loss + backward into grad (master layout); workspace from fsl_mlp_train_workspace(n)
 static int mlp_grad(const void *params, const void *X, const float *target, int n, float *loss_dev, void *workspace,

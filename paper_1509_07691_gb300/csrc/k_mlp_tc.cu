@@ -1,0 +1,304 @@
+// k_mlp_tc.cu -- forward pass of the learned-curvature MLP (125 -> 128 -> 128
+// -> 1, GELU, BF16 weights, FP32 accumulate; see k_mlp.cu) over a batch of
+// stencils on the 5th-generation tensor cores: tcgen05.mma with both operands
+// in shared memory and the FP32 accumulators in tensor memory (TMEM).
+//
+// One CTA (8 warps) per 128-row tile of the batch, persistent over tiles:
+//   layer 1  D1[128 x 128] = X[128 x 128] W1^T   (8 MMAs, M = N = 128, K = 16)
+//   epilogue tcgen05.ld of D1 (warp w reads TMEM lanes 32 (w % 4) .. + 31, the
+//            column half w / 4), + b1, GELU, BF16 -> H[128 x 128] in shared
+//            memory, the A operand of layer 2
+//   layer 2  D2 = H W2^T, epilogue + b2, GELU, dot with w3, + b3 -> y
+// Operands are stored K-major in the canonical no-swizzle layout: core
+// matrices of 8 rows x 16 bytes (8 BF16 along K), core (r8, k8) of a
+// 128 x 128 tile at byte (r8 * 16 + k8) * 128.  Completion of the MMAs is
+// signalled to an mbarrier by tcgen05.commit; every wait on it is bounded
+// and, when it runs out, records FSL_ETIMEOUT, skips the remaining tiles and
+// still frees the tensor memory.
+#include <math.h>
+
+#include "fsl_internal.cuh"
+
+namespace fslk {
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr int TILE = 128;
+constexpr int TMEM_COLS = 256;                 // D1 in columns 0..127, D2 in 128..255
+constexpr uint32_t CORE_K = 128;               // byte stride between core matrices along K
+constexpr uint32_t CORE_MN = 16 * 128;         // byte stride between 8-row groups
+constexpr int MB_BIAS_TC = 32896 * 2;          // byte offset of the FP32 biases in the packed block
+constexpr long long WAIT_LIMIT = 1ll << 26;    // try_wait polls before a wait gives up
+
+struct TcSmem {
+    __nv_bfloat16 W1[TILE * TILE];
+    __nv_bfloat16 W2[TILE * TILE];
+    __nv_bfloat16 X[TILE * TILE];
+    __nv_bfloat16 H[TILE * TILE];
+    float b1[TILE], b2[TILE], w3[TILE];
+    float ypart[TILE];
+    float b3;
+    uint32_t tmem_base;
+    unsigned long long mbar;
+    int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (r, k) of a 128 x 128 K-major tile in the canonical layout
+__device__ __forceinline__ uint32_t tile_off(int r, int k) {
+    return (uint32_t)(r >> 3) * CORE_MN + (uint32_t)(k >> 3) * CORE_K + (uint32_t)(r & 7) * 16 + (uint32_t)(k & 7) * 2;
+}
+
+// shared-memory matrix descriptor: start, leading and stride byte offsets
+// (>> 4), descriptor version 1 (bits 46-47), no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TILE >> 3) << 17) |
+                           ((uint32_t)(TILE >> 4) << 24);
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// bounded wait for the completion of the phase with the given parity
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+__device__ __forceinline__ float gelu_tc(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// copy a row-major [128][128] BF16 matrix (row stride ld elements) into the
+// canonical tile layout, 16 bytes at a time; rows >= nrows are zero
+__device__ __forceinline__ void load_tile(char *tile, const __nv_bfloat16 *src, long long ld, int nrows) {
+    for (int c = threadIdx.x; c < TILE * TILE / 8; c += blockDim.x) {
+        const int r = c >> 4, k8 = c & 15;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (r < nrows) v = *reinterpret_cast<const uint4 *>(src + (long long)r * ld + k8 * 8);
+        *reinterpret_cast<uint4 *>(tile + tile_off(r, k8 * 8)) = v;
+    }
+}
+
+}  // namespace
+
+// Descriptors: leading byte offset = stride between core matrices along K,
+// stride byte offset = stride between 8-row groups (checked against the
+// mma.sync network: identical pre-activations).
+template <bool STORE>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_forward_tc(const uint8_t *params, const __nv_bfloat16 *X, int n,
+                                                                  float *y, float *z1, float *z2, int *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TcSmem &s = *reinterpret_cast<TcSmem *>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lbo = CORE_K, sbo = CORE_MN;
+    // weights, biases
+    const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(params);
+    const float *bias = reinterpret_cast<const float *>(params + MB_BIAS_TC);
+    load_tile(reinterpret_cast<char *>(s.W1), wb, TILE, TILE);
+    load_tile(reinterpret_cast<char *>(s.W2), wb + TILE * TILE, TILE, TILE);
+    for (int e = threadIdx.x; e < TILE; e += blockDim.x) {
+        s.b1[e] = bias[e];
+        s.b2[e] = bias[TILE + e];
+        s.w3[e] = __bfloat162float(wb[2 * TILE * TILE + e]);
+    }
+    if (threadIdx.x == 0) {
+        s.b3 = bias[2 * TILE];
+        s.abort = 0;
+        mbar_init(&s.mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s.tmem_base;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;  // this warp's TMEM lanes
+    const int row = 32 * (warp & 3) + lane;                         // tile row of this thread
+    const int col0 = 64 * (warp >> 2);                              // its column half
+    const uint32_t aX = smem_u32(s.X), aH = smem_u32(s.H), aW1 = smem_u32(s.W1), aW2 = smem_u32(s.W2);
+    uint32_t phase = 0;
+    for (long long t0 = (long long)blockIdx.x * TILE; t0 < n; t0 += (long long)gridDim.x * TILE) {
+        const int rows = (int)min((long long)TILE, n - t0);
+        load_tile(reinterpret_cast<char *>(s.X), X + t0 * TILE, TILE, rows);
+        proxy_fence();
+        __syncthreads();
+        // ---- layer 1
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < TILE / 16; ++kk)
+                tc_mma(tmem, smem_desc(aX + kk * 2 * CORE_K, lbo, sbo), smem_desc(aW1 + kk * 2 * CORE_K, lbo, sbo),
+                       kk > 0);
+            tc_commit(&s.mbar);
+        }
+        if (__syncthreads_or(mbar_wait(&s.mbar, phase) ? 0 : 1)) {
+            if (threadIdx.x == 0) set_status(status, FSL_ETIMEOUT);
+            break;
+        }
+        phase ^= 1;
+        tc_fence_after();
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            const int c = col0 + 16 * cc;
+            float v[16];
+            tc_ld16(tmem + lane_base + c, v);
+            uint32_t h[8];
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) {
+                const float za = v[e] + s.b1[c + e], zb = v[e + 1] + s.b1[c + e + 1];
+                if (STORE && row < rows) *reinterpret_cast<float2 *>(z1 + (t0 + row) * TILE + c + e) = make_float2(za, zb);
+                h[e >> 1] = pack2(gelu_tc(za), gelu_tc(zb));
+            }
+            *reinterpret_cast<uint4 *>(reinterpret_cast<char *>(s.H) + tile_off(row, c)) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(reinterpret_cast<char *>(s.H) + tile_off(row, c + 8)) = make_uint4(h[4], h[5], h[6], h[7]);
+        }
+        tc_fence_before();
+        proxy_fence();
+        __syncthreads();
+        // ---- layer 2
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < TILE / 16; ++kk)
+                tc_mma(tmem + TILE, smem_desc(aH + kk * 2 * CORE_K, lbo, sbo), smem_desc(aW2 + kk * 2 * CORE_K, lbo, sbo),
+                       kk > 0);
+            tc_commit(&s.mbar);
+        }
+        if (__syncthreads_or(mbar_wait(&s.mbar, phase) ? 0 : 1)) {
+            if (threadIdx.x == 0) set_status(status, FSL_ETIMEOUT);
+            break;
+        }
+        phase ^= 1;
+        tc_fence_after();
+        float yp = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            const int c = col0 + 16 * cc;
+            float v[16];
+            tc_ld16(tmem + TILE + lane_base + c, v);
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) {
+                const float za = v[e] + s.b2[c + e], zb = v[e + 1] + s.b2[c + e + 1];
+                if (STORE && row < rows) *reinterpret_cast<float2 *>(z2 + (t0 + row) * TILE + c + e) = make_float2(za, zb);
+                yp += gelu_tc(za) * s.w3[c + e] + gelu_tc(zb) * s.w3[c + e + 1];
+            }
+        }
+        if (warp >= 4) s.ypart[row] = yp;
+        tc_fence_before();
+        __syncthreads();
+        if (warp < 4 && row < rows) y[t0 + row] = yp + s.ypart[row] + s.b3;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+size_t mlp_tc_smem() { return sizeof(TcSmem) + 1024; }
+
+// sticky status of the tensor-core kernels (a bounded wait that ran out)
+__device__ int g_mlp_tc_status;
+
+namespace {
+int *status_ptr() {  // device address of g_mlp_tc_status, looked up once per device
+    static int *ptr[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!ptr[dev] && cudaGetSymbolAddress((void **)&ptr[dev], g_mlp_tc_status) != cudaSuccess) ptr[dev] = nullptr;
+    return ptr[dev];
+}
+}  // namespace
+
+// launch on at most one CTA per SM (the tiles and the weights take about
+// 133 KB of shared memory), persistent over the 128-row tiles
+int launch_mlp_forward_tc(const uint8_t *params, const __nv_bfloat16 *X, int n, float *y, float *z1, float *z2,
+                          cudaStream_t s) {
+    int *st = status_ptr();
+    if (!st) return FSL_ECUDA;
+    const size_t sm = mlp_tc_smem();
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = (n + TILE - 1) / TILE;
+    const int grid = tiles < sms ? (tiles > 0 ? tiles : 1) : sms;
+    if (z1) {
+        if (cudaFuncSetAttribute(k_mlp_forward_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+            return FSL_ECUDA;
+        k_mlp_forward_tc<true><<<grid, TC_THREADS, sm, s>>>(params, X, n, y, z1, z2, st);
+    } else {
+        if (cudaFuncSetAttribute(k_mlp_forward_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+            return FSL_ECUDA;
+        k_mlp_forward_tc<false><<<grid, TC_THREADS, sm, s>>>(params, X, n, y, z1, z2, st);
+    }
+    return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
+}
+
+int mlp_tc_status(bool reset) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_mlp_tc_status, sizeof v) != cudaSuccess) return FSL_ECUDA;
+    if (reset) {
+        const int zero = 0;
+        if (cudaMemcpyToSymbol(g_mlp_tc_status, &zero, sizeof zero) != cudaSuccess) return FSL_ECUDA;
+    }
+    return v;
+}
+
+}  // namespace fslk

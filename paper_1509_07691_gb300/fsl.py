@@ -71,6 +71,7 @@ _SIGNATURES = {
     "fsl_mlp_stencils": (ctypes.c_int, [ctypes.c_int] + [ctypes.c_void_p] * 5 + [ctypes.c_int, ctypes.c_float,
                                                                                    ctypes.c_uint64] + [ctypes.c_void_p] * 3),
     "fsl_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),
+    "fsl_mlp_status": (ctypes.c_int, [ctypes.c_int]),
     "fsl_mlp_train_workspace": (ctypes.c_size_t, [ctypes.c_int]),
     "fsl_mlp_gradients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] +
                           [ctypes.c_void_p] * 4),
@@ -408,6 +409,11 @@ class Mlp:
         check(lib().fsl_mlp_forward(_ptr(self.params), _ptr(X), n, _ptr(y), _ptr(z1), _ptr(z2),
                                     _stream_handle(self.stream)), "fsl_mlp_forward")
         return (y, z1, z2) if keep else y
+
+    @staticmethod
+    def status(reset: bool = False) -> int:
+        """Sticky status of the tensor-core MLP kernels (0, or FSL_ETIMEOUT)."""
+        return lib().fsl_mlp_status(1 if reset else 0)
 
     def gradients(self, X, target):
         n = X.shape[0]

@@ -75,6 +75,7 @@ def test_forward_matches_oracle(F, M):
     # the stored pre-activations agree too
     y2, z1, z2 = net.forward(X, keep=True)
     assert np.array_equal(y2.cpu().numpy(), y)
+    assert F.Mlp.status() == 0  # no tensor-core wait ran out
     _, a = M.forward(w, phi)
     assert np.max(np.abs(z1.cpu().numpy() - a["z1"])) <= 1e-3
 
