@@ -250,7 +250,11 @@ int fsl_mlp_status(int reset);
 size_t fsl_mlp_train_workspace(int n);
 
 /* Gradients (master layout) of loss = (1/n) sum w (y - t)^2, w = 1/(t^2 + 7e-5),
- * and the loss itself (one float, device; may be NULL).  Asynchronous. */
+ * and the loss itself (one float, device; may be NULL).  The weight gradients
+ * dW1 = d1^T x and dW2 = d2^T h1 run on the tcgen05 tensor cores with the
+ * deltas rounded to BF16 and FP32 accumulation, one 128-sample chunk per CTA,
+ * the chunks summed in a fixed order; the deltas and bias gradients in FP32.
+ * Asynchronous. */
 int fsl_mlp_gradients(const void *params, const void *X, const float *target, int n, float *grad, float *loss_dev,
                       void *workspace, void *stream);
 

@@ -245,6 +245,13 @@ void launch_mlp_curv(const Dev &d, float *kappa_out, cudaStream_t s);
 int launch_mlp_forward_tc(const uint8_t *params, const __nv_bfloat16 *X, int n, float *y, float *z1, float *z2,
                           cudaStream_t s);
 int mlp_tc_status(bool reset);
+// weight gradients of the MLP on the tcgen05 tensor cores (k_mlp_tc.cu);
+// partial holds mlp_wgrad_partial_floats(n) floats
+size_t mlp_wgrad_partial_floats(int n);
+int launch_mlp_delta_tc(const uint8_t *params, const float *y, const float *target, int n, const float *z1,
+                        const float *z2, float *d1, float *d2, float *d3, cudaStream_t s);
+int launch_mlp_wgrad_tc(const __nv_bfloat16 *X, const float *z1, const float *d1, const float *d2, int n, float *partial,
+                        float *gW1, float *gW2, cudaStream_t s);
 void launch_fin_frozen(const Dev &d, cudaStream_t s);
 
 int max_partials();

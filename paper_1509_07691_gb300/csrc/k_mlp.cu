@@ -149,104 +149,48 @@ __device__ void warp_mlp(const MlpSmem &s, const __nv_bfloat16 *Xw, float &y_lo,
 
 // ---- backward (FP32): deltas, then weight gradients ------------------------
 // loss = (1/n) sum w (y - t)^2, w = 1/(t^2 + 7e-5)
-constexpr int DT = 32;  // samples per block in k_mlp_delta
+// bias gradients and dw3 = sum_n d3 h2, db3 = sum_n d3: partial sums over
+// chunks of VG_ROWS samples (block per chunk, thread per output), then a
+// fixed-order sum over the chunks
+constexpr int VG_ROWS = 16;
 
-__global__ void __launch_bounds__(MK) k_mlp_delta(const uint8_t *params, const float *y, const float *target, int n,
-                                                  const float *z1, const float *z2, float *d1, float *d2, float *d3) {
-    extern __shared__ __align__(16) uint8_t smem_raw[];
-    float *W2s = reinterpret_cast<float *>(smem_raw);  // [128][129]
-    float *D2s = W2s + MK * (MK + 1);                  // [DT][128]
-    __shared__ float d3s[DT];
-    const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(params);
-    for (int e = threadIdx.x; e < MK * MK; e += blockDim.x) W2s[(e / MK) * (MK + 1) + e % MK] = __bfloat162float(wb[MK * MK + e]);
-    const float w3 = __bfloat162float(wb[2 * MK * MK + threadIdx.x]);
+__global__ void __launch_bounds__(MK) k_mlp_vgrad_part(const float *z2, const float *d1, const float *d2,
+                                                       const float *d3, int n, float *vpart) {
     const int i = threadIdx.x;
-    for (long long base = (long long)blockIdx.x * DT; base < n; base += (long long)gridDim.x * DT) {
-        __syncthreads();
-        if (i < DT) {
-            const long long r = base + i;
-            float v = 0.f;
-            if (r < n) {
-                const float tt = target[r];
-                v = 2.0f * (y[r] - tt) / ((tt * tt + 7e-5f) * (float)n);
-                d3[r] = v;
-            }
-            d3s[i] = v;
-        }
-        __syncthreads();
-        for (int sidx = 0; sidx < DT; ++sidx) {
-            const long long r = base + sidx;
-            const float v = r < n ? d3s[sidx] * w3 * gelu_grad(z2[r * MK + i]) : 0.f;
-            D2s[sidx * MK + i] = v;
-            if (r < n) d2[r * MK + i] = v;
-        }
-        __syncthreads();
-        for (int sidx = 0; sidx < DT; ++sidx) {
-            const long long r = base + sidx;
-            if (r >= n) break;
-            float acc = 0.f;
-#pragma unroll 8
-            for (int o = 0; o < MK; ++o) acc += W2s[o * (MK + 1) + i] * D2s[sidx * MK + o];
-            d1[r * MK + i] = acc * gelu_grad(z1[r * MK + i]);
-        }
-    }
-}
-
-// dW[o][i] = sum_n A[n][o] B[n][i] for (A, B) = (d1, x) and (d2, h1); one
-// 32 x 32 tile per block over the whole batch (fixed summation order)
-__global__ void __launch_bounds__(256) k_mlp_wgrad(const __nv_bfloat16 *X, const float *z1, const float *d1,
-                                                   const float *d2, int n, float *grad) {
-    __shared__ float As[32][33], Bs[32][33];
-    const int mat = blockIdx.x / 16, tile = blockIdx.x % 16;
-    const int o0 = (tile / 4) * 32, i0 = (tile % 4) * 32;
-    const float *A = mat == 0 ? d1 : d2;
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-    for (long long nb = 0; nb < n; nb += 32) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-            const int r = e / 32, c = e % 32;
-            const long long row = nb + r;
-            float a = 0.f, b = 0.f;
-            if (row < n) {
-                a = A[row * MK + o0 + c];
-                if (mat == 0) b = __bfloat162float(X[row * MK + i0 + c]);
-                else b = __bfloat162float(__float2bfloat16_rn(gelu(z1[row * MK + i0 + c])));
-            }
-            As[r][c] = a;
-            Bs[r][c] = b;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int r = 0; r < 32; ++r) {
-            const float a0 = As[r][ty * 2], a1 = As[r][ty * 2 + 1];
-            const float b0 = Bs[r][tx * 2], b1 = Bs[r][tx * 2 + 1];
-            acc[0][0] += a0 * b0;
-            acc[0][1] += a0 * b1;
-            acc[1][0] += a1 * b0;
-            acc[1][1] += a1 * b1;
-        }
-    }
-    float *G = grad + (mat == 0 ? M_W1 : M_W2);
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b) G[(o0 + ty * 2 + a) * MK + i0 + tx * 2 + b] = acc[a][b];
-}
-
-// bias gradients and dw3 = sum_n d3 h2, db3 = sum_n d3 (thread per output)
-__global__ void __launch_bounds__(MK) k_mlp_vgrad(const float *z2, const float *d1, const float *d2, const float *d3,
-                                                  int n, float *grad) {
-    const int i = threadIdx.x;
+    const long long r0 = (long long)blockIdx.x * VG_ROWS, r1 = min((long long)n, r0 + VG_ROWS);
     float sb1 = 0.f, sb2 = 0.f, sw3 = 0.f, sb3 = 0.f;
-    for (long long r = 0; r < n; ++r) {
+    for (long long r = r0; r < r1; ++r) {
         sb1 += d1[r * MK + i];
         sb2 += d2[r * MK + i];
         sw3 += d3[r] * gelu(z2[r * MK + i]);
         if (i == 0) sb3 += d3[r];
     }
-    grad[M_B1 + i] = sb1;
-    grad[M_B2 + i] = sb2;
-    grad[M_W3 + i] = sw3;
-    if (i == 0) grad[M_B3] = sb3;
+    float *v = vpart + (size_t)blockIdx.x * 4 * MK;
+    v[i] = sb1;
+    v[MK + i] = sb2;
+    v[2 * MK + i] = sw3;
+    v[3 * MK + i] = i == 0 ? sb3 : 0.f;
+}
+
+// one block per gradient vector (db1, db2, dw3, db3), thread per output; the
+// chunk partials are summed in order, eight loads in flight per thread
+__global__ void __launch_bounds__(MK) k_mlp_vgrad_sum(const float *vpart, int nb, float *grad) {
+    const int i = threadIdx.x, vec = blockIdx.x;
+    const float *v = vpart + vec * MK + i;
+    float acc = 0.f;
+    int b = 0;
+    for (; b + 8 <= nb; b += 8) {
+        float t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = v[(size_t)(b + u) * 4 * MK];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += t[u];
+    }
+    for (; b < nb; ++b) acc += v[(size_t)b * 4 * MK];
+    if (vec == 0) grad[M_B1 + i] = acc;
+    else if (vec == 1) grad[M_B2 + i] = acc;
+    else if (vec == 2) grad[M_W3 + i] = acc;
+    else if (i == 0) grad[M_B3] = acc;
 }
 
 // loss (1/n) sum w (y - t)^2, fixed-order reduction in one block
@@ -540,10 +484,32 @@ extern "C" {
 size_t fsl_mlp_param_bytes(void) { return MB_BIAS + (size_t)(2 * MK + 1) * sizeof(float); }
 int fsl_mlp_master_count(void) { return M_COUNT; }
 
+// training workspace, in floats: z1, z2, d1, d2 ([n][128] each, first so that
+// their rows stay 16-byte aligned), y, d3, grad, the weight-gradient partials
+// of the tensor-core kernel and the bias-gradient partials, each 64-aligned
+struct TrainWs {
+    size_t z1, z2, d1, d2, y, d3, grad, wpart, vpart, total;
+};
+static size_t up64(size_t v) { return (v + 63) / 64 * 64; }
+static TrainWs train_ws(int n) {
+    TrainWs w;
+    size_t o = 0;
+    w.z1 = o; o += (size_t)n * MK;
+    w.z2 = o; o += (size_t)n * MK;
+    w.d1 = o; o += (size_t)n * MK;
+    w.d2 = o; o += (size_t)n * MK;
+    w.y = o; o = up64(o + n);
+    w.d3 = o; o = up64(o + n);
+    w.grad = o; o = up64(o + M_COUNT);
+    w.wpart = o; o = up64(o + mlp_wgrad_partial_floats(n));
+    w.vpart = o; o = up64(o + (size_t)((n + VG_ROWS - 1) / VG_ROWS) * 4 * MK);
+    w.total = o;
+    return w;
+}
+
 size_t fsl_mlp_train_workspace(int n) {
     if (n <= 0) return 0;
-    // y, z1, z2, d1, d2, d3, grad
-    return ((size_t)n * (1 + 4 * MK + 1) + M_COUNT) * sizeof(float) + 1024;
+    return train_ws(n).total * sizeof(float) + 1024;
 }
 
 int fsl_mlp_stencils(int n, const float *axes, const float *quat, const float *dir, const float *delta,
@@ -571,17 +537,20 @@ int fsl_mlp_status(int reset) { return mlp_tc_status(reset != 0); }
 static int mlp_grad(const void *params, const void *X, const float *target, int n, float *loss_dev, void *workspace,
                     float **grad_out, cudaStream_t s) {
     float *ws = static_cast<float *>(workspace);
-    float *y = ws, *z1 = y + n, *z2 = z1 + (size_t)n * MK, *d1 = z2 + (size_t)n * MK, *d2 = d1 + (size_t)n * MK;
-    float *d3 = d2 + (size_t)n * MK, *grad = d3 + n;
+    const TrainWs L = train_ws(n);
+    float *z1 = ws + L.z1, *z2 = ws + L.z2, *d1 = ws + L.d1, *d2 = ws + L.d2, *y = ws + L.y, *d3 = ws + L.d3;
+    float *grad = ws + L.grad;
     int rc = fsl_mlp_forward(params, X, n, y, z1, z2, s);
     if (rc != FSL_OK) return rc;
     if (loss_dev) k_mlp_loss<<<1, 256, 0, s>>>(y, target, n, loss_dev);
-    const size_t dsm = (size_t)(MK * (MK + 1) + DT * MK) * sizeof(float);
-    static const int gd = mlp_grid((const void *)k_mlp_delta, MK, dsm);
-    const int bd = (n + DT - 1) / DT;
-    k_mlp_delta<<<bd < gd ? bd : gd, MK, dsm, s>>>(static_cast<const uint8_t *>(params), y, target, n, z1, z2, d1, d2, d3);
-    k_mlp_wgrad<<<32, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(X), z1, d1, d2, n, grad);
-    k_mlp_vgrad<<<1, MK, 0, s>>>(z2, d1, d2, d3, n, grad);
+    rc = launch_mlp_delta_tc(static_cast<const uint8_t *>(params), y, target, n, z1, z2, d1, d2, d3, s);
+    if (rc != FSL_OK) return rc;
+    rc = launch_mlp_wgrad_tc(static_cast<const __nv_bfloat16 *>(X), z1, d1, d2, n, ws + L.wpart, grad + M_W1,
+                             grad + M_W2, s);
+    if (rc != FSL_OK) return rc;
+    const int nb = (n + VG_ROWS - 1) / VG_ROWS;
+    k_mlp_vgrad_part<<<nb, MK, 0, s>>>(z2, d1, d2, d3, n, ws + L.vpart);
+    k_mlp_vgrad_sum<<<4, MK, 0, s>>>(ws + L.vpart, nb, grad);
     *grad_out = grad;
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
 }

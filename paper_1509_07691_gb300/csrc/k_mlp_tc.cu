@@ -251,6 +251,229 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_forward_tc(const uint8_t 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// ---- weight gradients on the tensor cores -------------------------------------
+// dW1[o][i] = sum_b d1[b][o] x[b][i] and dW2[o][i] = sum_b d2[b][o] h1[b][i]
+// (h1 = bf16(gelu(z1)), as the forward feeds layer 2): one CTA per 128-sample
+// chunk of the batch and matrix, an MMA group with M = o, N = i, K = b over
+// the chunk (both operands staged transposed into the K-major tile, in BF16),
+// the 128 x 128 partial written to partial[mat][chunk]; k_mlp_wreduce sums
+// the chunks in a fixed order.
+struct WgSmem {
+    __nv_bfloat16 A[TILE * TILE];
+    __nv_bfloat16 B[TILE * TILE];
+    uint32_t tmem_base;
+    unsigned long long mbar;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_wgrad_tc(const __nv_bfloat16 *X, const float *z1, const float *d1,
+                                                               const float *d2, int n, float *partial, int *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    WgSmem &s = *reinterpret_cast<WgSmem *>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mat = blockIdx.y, chunk = blockIdx.x, nchunk = gridDim.x;
+    const long long b0 = (long long)chunk * TILE;
+    const int rows = (int)min((long long)TILE, n - b0);
+    const float *D = mat == 0 ? d1 : d2;
+    char *At = reinterpret_cast<char *>(s.A), *Bt = reinterpret_cast<char *>(s.B);
+    // A[o][b] = D[b0 + b][o], B[i][b] = x or h1 at [b0 + b][i]: thread per (b, 8 columns)
+    for (int c = threadIdx.x; c < TILE * TILE / 8; c += blockDim.x) {
+        const int b = c >> 4, c8 = (c & 15) * 8;
+        float av[8], bv[8];
+        if (b < rows) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(D + (b0 + b) * TILE + c8);
+            const float4 a1 = *reinterpret_cast<const float4 *>(D + (b0 + b) * TILE + c8 + 4);
+            av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w; av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
+            if (mat == 0) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) bv[e] = __bfloat162float(X[(b0 + b) * TILE + c8 + e]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) bv[e] = gelu_tc(z1[(b0 + b) * TILE + c8 + e]);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) av[e] = bv[e] = 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            *reinterpret_cast<__nv_bfloat16 *>(At + tile_off(c8 + e, b)) = __float2bfloat16_rn(av[e]);
+            *reinterpret_cast<__nv_bfloat16 *>(Bt + tile_off(c8 + e, b)) = __float2bfloat16_rn(bv[e]);
+        }
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&s.mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem_base)),
+                     "r"(TILE)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s.tmem_base;
+    if (threadIdx.x == 0) {
+        const uint32_t aA = smem_u32(s.A), aB = smem_u32(s.B);
+#pragma unroll
+        for (int kk = 0; kk < TILE / 16; ++kk)
+            tc_mma(tmem, smem_desc(aA + kk * 2 * CORE_K, CORE_K, CORE_MN), smem_desc(aB + kk * 2 * CORE_K, CORE_K, CORE_MN),
+                   kk > 0);
+        tc_commit(&s.mbar);
+    }
+    const bool ok = !__syncthreads_or(mbar_wait(&s.mbar, 0) ? 0 : 1);
+    if (ok) {
+        tc_fence_after();
+        const int o = 32 * (warp & 3) + lane, col0 = 64 * (warp >> 2);
+        float *P = partial + ((size_t)mat * nchunk + chunk) * TILE * TILE + (size_t)o * TILE;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            const int c = col0 + 16 * cc;
+            float v[16];
+            tc_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c, v);
+#pragma unroll
+            for (int e = 0; e < 16; e += 4) *reinterpret_cast<float4 *>(P + c + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+        }
+    } else if (threadIdx.x == 0) {
+        set_status(status, FSL_ETIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TILE) : "memory");
+}
+
+// ---- deltas on the tensor cores ------------------------------------------------
+// d3 = dL/dy = 2 (y - t) / ((t^2 + 7e-5) n), d2 = d3 w3 gelu'(z2) (FP32, as
+// stored for the weight and bias gradients), d1 = (d2 W2) gelu'(z1) with the
+// product d2 W2 as an MMA: M = sample b, N = i, K = o, d2 rounded to BF16,
+// W2 staged transposed (B[i][o] = W2[o][i]).  One CTA per 128-sample chunk.
+__device__ __forceinline__ float gelu_grad_tc(float x) {
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+struct DtSmem {
+    __nv_bfloat16 A[TILE * TILE];
+    __nv_bfloat16 B[TILE * TILE];
+    float w3[TILE];
+    float d3[TILE];
+    uint32_t tmem_base;
+    unsigned long long mbar;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_delta_tc(const uint8_t *params, const float *y, const float *target,
+                                                               int n, const float *z1, const float *z2, float *d1,
+                                                               float *d2, float *d3, int *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    DtSmem &s = *reinterpret_cast<DtSmem *>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long b0 = (long long)blockIdx.x * TILE;
+    const int rows = (int)min((long long)TILE, n - b0);
+    const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(params);
+    char *At = reinterpret_cast<char *>(s.A), *Bt = reinterpret_cast<char *>(s.B);
+    if (threadIdx.x < TILE) {
+        const int b = threadIdx.x;
+        s.w3[b] = __bfloat162float(wb[2 * TILE * TILE + b]);
+        float v = 0.f;
+        if (b < rows) {
+            const float tt = target[b0 + b];
+            v = 2.0f * (y[b0 + b] - tt) / ((tt * tt + 7e-5f) * (float)n);
+            d3[b0 + b] = v;
+        }
+        s.d3[b] = v;
+    }
+    // B[i][o] = W2[o][i]: thread per (o, 8 consecutive i)
+    for (int c = threadIdx.x; c < TILE * TILE / 8; c += blockDim.x) {
+        const int o = c >> 4, i8 = (c & 15) * 8;
+        const uint4 v = *reinterpret_cast<const uint4 *>(wb + TILE * TILE + o * TILE + i8);
+        const __nv_bfloat16 *e8 = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) *reinterpret_cast<__nv_bfloat16 *>(Bt + tile_off(i8 + e, o)) = e8[e];
+    }
+    __syncthreads();
+    // d2 (FP32 to memory, BF16 into A[b][o])
+    for (int c = threadIdx.x; c < TILE * TILE / 8; c += blockDim.x) {
+        const int b = c >> 4, o8 = (c & 15) * 8;
+        uint32_t h[4];
+        if (b < rows) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = s.d3[b] * s.w3[o8 + e] * gelu_grad_tc(z2[(b0 + b) * TILE + o8 + e]);
+            *reinterpret_cast<float4 *>(d2 + (b0 + b) * TILE + o8) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4 *>(d2 + (b0 + b) * TILE + o8 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) h[e] = pack2(v[2 * e], v[2 * e + 1]);
+        } else {
+            h[0] = h[1] = h[2] = h[3] = 0u;
+        }
+        *reinterpret_cast<uint4 *>(At + tile_off(b, o8)) = make_uint4(h[0], h[1], h[2], h[3]);
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&s.mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem_base)),
+                     "r"(TILE)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s.tmem_base;
+    if (threadIdx.x == 0) {
+        const uint32_t aA = smem_u32(s.A), aB = smem_u32(s.B);
+#pragma unroll
+        for (int kk = 0; kk < TILE / 16; ++kk)
+            tc_mma(tmem, smem_desc(aA + kk * 2 * CORE_K, CORE_K, CORE_MN), smem_desc(aB + kk * 2 * CORE_K, CORE_K, CORE_MN),
+                   kk > 0);
+        tc_commit(&s.mbar);
+    }
+    const bool ok = !__syncthreads_or(mbar_wait(&s.mbar, 0) ? 0 : 1);
+    if (ok) {
+        tc_fence_after();
+        const int b = 32 * (warp & 3) + lane, col0 = 64 * (warp >> 2);
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            const int c = col0 + 16 * cc;
+            float v[16];
+            tc_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c, v);
+            if (b < rows) {
+                const float *zr = z1 + (b0 + b) * TILE + c;
+                float *dr = d1 + (b0 + b) * TILE + c;
+#pragma unroll
+                for (int e = 0; e < 16; e += 4)
+                    *reinterpret_cast<float4 *>(dr + e) =
+                        make_float4(v[e] * gelu_grad_tc(zr[e]), v[e + 1] * gelu_grad_tc(zr[e + 1]),
+                                    v[e + 2] * gelu_grad_tc(zr[e + 2]), v[e + 3] * gelu_grad_tc(zr[e + 3]));
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        set_status(status, FSL_ETIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TILE) : "memory");
+}
+
+// grad[off + e] = sum over chunks of partial[mat][chunk][e], chunks in order
+__global__ void __launch_bounds__(256) k_mlp_wreduce(const float *partial, int nchunk, float *gW1, float *gW2) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * TILE * TILE) return;
+    const int mat = e / (TILE * TILE), k = e % (TILE * TILE);
+    const float *P = partial + (size_t)mat * nchunk * TILE * TILE + k;
+    float acc = 0.f;
+    for (int c = 0; c < nchunk; ++c) acc += P[(size_t)c * TILE * TILE];
+    (mat == 0 ? gW1 : gW2)[k] = acc;
+}
+
 size_t mlp_tc_smem() { return sizeof(TcSmem) + 1024; }
 
 // sticky status of the tensor-core kernels (a bounded wait that ran out)
@@ -288,6 +511,32 @@ int launch_mlp_forward_tc(const uint8_t *params, const __nv_bfloat16 *X, int n, 
             return FSL_ECUDA;
         k_mlp_forward_tc<false><<<grid, TC_THREADS, sm, s>>>(params, X, n, y, z1, z2, st);
     }
+    return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
+}
+
+size_t mlp_wgrad_partial_floats(int n) { return (size_t)2 * ((n + TILE - 1) / TILE) * TILE * TILE; }
+
+int launch_mlp_wgrad_tc(const __nv_bfloat16 *X, const float *z1, const float *d1, const float *d2, int n, float *partial,
+                        float *gW1, float *gW2, cudaStream_t s) {
+    int *st = status_ptr();
+    if (!st) return FSL_ECUDA;
+    const int nchunk = (n + TILE - 1) / TILE;
+    const size_t sm = sizeof(WgSmem) + 1024;
+    if (cudaFuncSetAttribute(k_mlp_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return FSL_ECUDA;
+    k_mlp_wgrad_tc<<<dim3(nchunk, 2), TC_THREADS, sm, s>>>(X, z1, d1, d2, n, partial, st);
+    k_mlp_wreduce<<<(2 * TILE * TILE + 255) / 256, 256, 0, s>>>(partial, nchunk, gW1, gW2);
+    return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
+}
+
+int launch_mlp_delta_tc(const uint8_t *params, const float *y, const float *target, int n, const float *z1,
+                        const float *z2, float *d1, float *d2, float *d3, cudaStream_t s) {
+    int *st = status_ptr();
+    if (!st) return FSL_ECUDA;
+    const size_t sm = sizeof(DtSmem) + 1024;
+    if (cudaFuncSetAttribute(k_mlp_delta_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return FSL_ECUDA;
+    k_mlp_delta_tc<<<(n + TILE - 1) / TILE, TC_THREADS, sm, s>>>(params, y, target, n, z1, z2, d1, d2, d3, st);
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
 }
 
