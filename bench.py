@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--mlp-train", type=int, default=10_000_000, help="training stencils of the learned curvature")
     ap.add_argument("--mlp-epochs", type=int, default=2)
+    ap.add_argument("--mlp-only", action="store_true",
+                    help="run only the MLP training section (no in-step inference) and print it")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint-window section (one evaluation, no checks) and print it")
     return ap.parse_args()
@@ -358,7 +360,7 @@ def side_workload(F, S, name, storage, steps, stream, flush, peaks, seed):
     return out
 
 
-def learned_curvature(F, S, stream, flush, peaks, seed, n_train, epochs, steps):
+def learned_curvature(F, S, stream, flush, peaks, seed, n_train, epochs, steps, inference=True):
     """Config-5 form: train the network on GPU-made stencils, then run the
     384^3 two-droplet coalescence with FSL_CURV_MLP (LSQR judge, 5 %)."""
     import torch
@@ -400,6 +402,8 @@ def learned_curvature(F, S, stream, flush, peaks, seed, n_train, epochs, steps):
     Xt, tt = F.mlp_stencils(q, sub=8, noise=1e-3, noise_seed=seed + 5)
     yt = net.forward(Xt).cpu().numpy()
     out["heldout"] = {"params": q, "noise_seed": seed + 5, "truth": tt.cpu().numpy(), "mlp": yt}
+    if not inference:
+        return out
     # inference inside FSLBM
     w = S.workload("coalescence384", seed=seed)
     P = F.make_params(w["shape"], collision=F.BGK, curv_model=F.CURV_MLP, tau=w["tau"], sigma=w["sigma"],
@@ -722,6 +726,16 @@ def run_fsl(args):
 
 def main():
     args = parse()
+    if args.mlp_only:
+        import torch
+        from paper_1509_07691_gb300 import build, synthetic as S
+        build.build()
+        from paper_1509_07691_gb300 import fsl as F
+        lc = learned_curvature(F, S, torch.cuda.current_stream(), None, {}, S.SEED, args.mlp_train, args.mlp_epochs, 0,
+                               inference=False)
+        lc.pop("heldout")
+        print(json.dumps({"learned_curvature": lc}))
+        return
     if args.adjoint_only:
         import torch
         from paper_1509_07691_gb300 import build, synthetic as S

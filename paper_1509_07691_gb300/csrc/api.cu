@@ -36,7 +36,7 @@ constexpr size_t ALIGN = 256;
 size_t up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t normal, rho, excess, iflist0, iflist1, fill, empty, newgas, liq2if, slow, seg_active, seg_list, counts,
+    size_t normal, rho, excess, rmark, iflist0, iflist1, fill, empty, newgas, liq2if, slow, seg_active, seg_list, counts,
         lost, status, partial, stats, mass_out, total;
 };
 
@@ -49,6 +49,7 @@ Layout layout(const fsl_params &p) {
     L.normal = o; o += up(N * sizeof(float4));
     L.rho = o; o += up(N * sizeof(float));
     L.excess = o; o += up(N * sizeof(float));
+    L.rmark = o; o += up(N);
     L.iflist0 = o; o += up(N * sizeof(int));
     L.iflist1 = o; o += up(N * sizeof(int));
     L.fill = o; o += up(N * sizeof(int));
@@ -103,6 +104,7 @@ Dev make_dev(const fsl_params &p, const fsl_fields &f) {
     d.normal = reinterpret_cast<float4 *>(ws + L.normal);
     d.rho = reinterpret_cast<float *>(ws + L.rho);
     d.excess = reinterpret_cast<float *>(ws + L.excess);
+    d.rmark = reinterpret_cast<uint8_t *>(ws + L.rmark);
     d.iflist = reinterpret_cast<int *>(ws + L.iflist0);
     d.iflist_next = reinterpret_cast<int *>(ws + L.iflist1);
     d.seg_active = reinterpret_cast<uint8_t *>(ws + L.seg_active);
@@ -379,6 +381,7 @@ int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *ph
         if (cudaMemsetAsync(c->base.normal, 0, N * sizeof(float4), s) != cudaSuccess) break;
         if (cudaMemsetAsync(fields->kappa, 0, N * sizeof(float), s) != cudaSuccess) break;
         if (cudaMemsetAsync(c->base.seg_active, 0, c->base.nseg, s) != cudaSuccess) break;
+        if (cudaMemsetAsync(c->base.rmark, 0, N, s) != cudaSuccess) break;
         Dev d = dev_for(c, 1);  // fdst = f[0]
         launch_init_types(d, obs, fields->flags[1], s);
         Dev d0 = dev_for(c, 0);
@@ -403,6 +406,7 @@ int fsl_refresh(fsl_ctx *c) {
     Dev d = dev_for(c, c->parity);
     CK(cudaMemsetAsync(d.counts, 0, C_NCOUNT * sizeof(int), c->stream));
     CK(cudaMemsetAsync(d.seg_active, 0, d.nseg, c->stream));
+    CK(cudaMemsetAsync(d.rmark, 0, d.N, c->stream));
     launch_refresh(d, c->stream);
     launch_seg_compact(d, c->stream);
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;

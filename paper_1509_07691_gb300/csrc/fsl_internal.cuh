@@ -59,6 +59,37 @@ constexpr int SEG = 32;
 // status word values (sticky; first error wins)
 __device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
 
+// Programmatic dependent launch along the serial chain of a step.  A kernel
+// started with launch_pdl may be dispatched while its predecessor on the
+// stream is still running: it calls pdl_wait() before anything else (the wait
+// returns once the predecessor grid has completed and its writes are
+// visible), then pdl_trigger() so that its own successor can be dispatched
+// early in turn.  Both are no-ops in a kernel launched the ordinary way.
+#ifndef FSL_PDL
+#define FSL_PDL 1
+#endif
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+    pdl_wait();
+    pdl_trigger();
+}
+
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), int grid, int block, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = FSL_PDL;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // kernel argument block (passed by value)
 struct Dev {
     int nx, ny, nz;
@@ -75,6 +106,7 @@ struct Dev {
     int *fill, *empty, *newgas, *liq2if;
     int *slow;         // interface cells whose LSQR fit takes the general path
     uint8_t *seg_active;
+    uint8_t *rmark;    // 1: the cell receives excess mass in this step's final update (0 between steps)
     int *seg_list;
     int nsegx, nseg;
     int *counts;

@@ -37,6 +37,7 @@ __device__ __forceinline__ float phi_ext(const Dev &d, int x, int y, int z) {
 // lists, general-path LSQR list, FP64 re-solves, next interface list); every
 // later kernel of the step is ordered after it on the stream.
 __global__ void __launch_bounds__(LIST_THREADS) k_normals(Dev d) {
+    pdl_enter();
     int cnt[1];
     block_counts<1>(d.counts, {d.cif}, cnt);
     const int n = cnt[0];

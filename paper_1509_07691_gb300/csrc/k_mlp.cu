@@ -150,41 +150,65 @@ __device__ void warp_mlp(const MlpSmem &s, const __nv_bfloat16 *Xw, float &y_lo,
 // ---- backward (FP32): deltas, then weight gradients ------------------------
 // loss = (1/n) sum w (y - t)^2, w = 1/(t^2 + 7e-5)
 // bias gradients and dw3 = sum_n d3 h2, db3 = sum_n d3: partial sums over
-// chunks of VG_ROWS samples (block per chunk, thread per output), then a
-// fixed-order sum over the chunks
-constexpr int VG_ROWS = 16;
+// chunks of VG_ROWS samples, then a fixed-order sum over the chunks.  A chunk
+// is one block of VG_GROUPS x 128 threads: group g sums rows [16 g, 16 g + 16)
+// of the chunk with all sixteen rows' loads in flight (a rolled loop waited
+// out one DRAM round trip per row), and group 0 adds the groups in order.
+constexpr int VG_GROUPS = 4;
+constexpr int VG_SUB = 16;
+constexpr int VG_ROWS = VG_GROUPS * VG_SUB;
 
-__global__ void __launch_bounds__(MK) k_mlp_vgrad_part(const float *z2, const float *d1, const float *d2,
-                                                       const float *d3, int n, float *vpart) {
-    const int i = threadIdx.x;
-    const long long r0 = (long long)blockIdx.x * VG_ROWS, r1 = min((long long)n, r0 + VG_ROWS);
-    float sb1 = 0.f, sb2 = 0.f, sw3 = 0.f, sb3 = 0.f;
-    for (long long r = r0; r < r1; ++r) {
-        sb1 += d1[r * MK + i];
-        sb2 += d2[r * MK + i];
-        sw3 += d3[r] * gelu(z2[r * MK + i]);
-        if (i == 0) sb3 += d3[r];
+__global__ void __launch_bounds__(VG_GROUPS * MK) k_mlp_vgrad_part(const float *z2, const float *d1,
+                                                                   const float *d2, const float *d3, int n,
+                                                                   float *vpart) {
+    __shared__ float red[VG_GROUPS - 1][4][MK];
+    const int i = threadIdx.x % MK, g = threadIdx.x / MK;
+    const long long r0 = (long long)blockIdx.x * VG_ROWS + g * VG_SUB;
+    const int m = (int)max(0LL, min((long long)VG_SUB, (long long)n - r0));
+    float a1[VG_SUB], a2[VG_SUB], az[VG_SUB], a3[VG_SUB];
+#pragma unroll
+    for (int u = 0; u < VG_SUB; ++u) {
+        const bool ok = u < m;
+        const long long r = r0 + u;
+        a1[u] = ok ? d1[r * MK + i] : 0.f;
+        a2[u] = ok ? d2[r * MK + i] : 0.f;
+        az[u] = ok ? z2[r * MK + i] : 0.f;
+        a3[u] = ok ? d3[r] : 0.f;
     }
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < VG_SUB; ++u) {
+        s[0] += a1[u];
+        s[1] += a2[u];
+        s[2] += a3[u] * gelu(az[u]);
+        s[3] += a3[u];
+    }
+    if (g > 0)
+        for (int k = 0; k < 4; ++k) red[g - 1][k][i] = s[k];
+    __syncthreads();
+    if (g > 0) return;
+    for (int h = 0; h < VG_GROUPS - 1; ++h)
+        for (int k = 0; k < 4; ++k) s[k] += red[h][k][i];
     float *v = vpart + (size_t)blockIdx.x * 4 * MK;
-    v[i] = sb1;
-    v[MK + i] = sb2;
-    v[2 * MK + i] = sw3;
-    v[3 * MK + i] = i == 0 ? sb3 : 0.f;
+    v[i] = s[0];
+    v[MK + i] = s[1];
+    v[2 * MK + i] = s[2];
+    v[3 * MK + i] = i == 0 ? s[3] : 0.f;
 }
 
 // one block per gradient vector (db1, db2, dw3, db3), thread per output; the
-// chunk partials are summed in order, eight loads in flight per thread
+// chunk partials are summed in order, sixteen loads in flight per thread
 __global__ void __launch_bounds__(MK) k_mlp_vgrad_sum(const float *vpart, int nb, float *grad) {
     const int i = threadIdx.x, vec = blockIdx.x;
     const float *v = vpart + vec * MK + i;
     float acc = 0.f;
     int b = 0;
-    for (; b + 8 <= nb; b += 8) {
-        float t[8];
+    for (; b + 16 <= nb; b += 16) {
+        float t[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) t[u] = v[(size_t)(b + u) * 4 * MK];
+        for (int u = 0; u < 16; ++u) t[u] = v[(size_t)(b + u) * 4 * MK];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc += t[u];
+        for (int u = 0; u < 16; ++u) acc += t[u];
     }
     for (; b < nb; ++b) acc += v[(size_t)b * 4 * MK];
     if (vec == 0) grad[M_B1 + i] = acc;
@@ -194,16 +218,18 @@ __global__ void __launch_bounds__(MK) k_mlp_vgrad_sum(const float *vpart, int nb
 }
 
 // loss (1/n) sum w (y - t)^2, fixed-order reduction in one block
-__global__ void __launch_bounds__(256) k_mlp_loss(const float *y, const float *target, int n, float *loss) {
-    __shared__ double red[256];
+// Each term in FP32 (the FP64 divide rate of one SM made this kernel the
+// slowest of a training step), summed in FP64 in a fixed order.
+__global__ void __launch_bounds__(1024) k_mlp_loss(const float *y, const float *target, int n, float *loss) {
+    __shared__ double red[1024];
     double s = 0.0;
     for (long long r = threadIdx.x; r < n; r += blockDim.x) {
-        const double tt = target[r], e = (double)y[r] - tt;
-        s += e * e / (tt * tt + 7e-5);
+        const float tt = target[r], e = y[r] - tt;
+        s += (double)(e * e / (tt * tt + 7e-5f));
     }
     red[threadIdx.x] = s;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
+    for (int w = 512; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
@@ -542,14 +568,14 @@ static int mlp_grad(const void *params, const void *X, const float *target, int 
     float *grad = ws + L.grad;
     int rc = fsl_mlp_forward(params, X, n, y, z1, z2, s);
     if (rc != FSL_OK) return rc;
-    if (loss_dev) k_mlp_loss<<<1, 256, 0, s>>>(y, target, n, loss_dev);
+    if (loss_dev) k_mlp_loss<<<1, 1024, 0, s>>>(y, target, n, loss_dev);
     rc = launch_mlp_delta_tc(static_cast<const uint8_t *>(params), y, target, n, z1, z2, d1, d2, d3, s);
     if (rc != FSL_OK) return rc;
     rc = launch_mlp_wgrad_tc(static_cast<const __nv_bfloat16 *>(X), z1, d1, d2, n, ws + L.wpart, grad + M_W1,
                              grad + M_W2, s);
     if (rc != FSL_OK) return rc;
     const int nb = (n + VG_ROWS - 1) / VG_ROWS;
-    k_mlp_vgrad_part<<<nb, MK, 0, s>>>(z2, d1, d2, d3, n, ws + L.vpart);
+    k_mlp_vgrad_part<<<nb, VG_GROUPS * MK, 0, s>>>(z2, d1, d2, d3, n, ws + L.vpart);
     k_mlp_vgrad_sum<<<4, MK, 0, s>>>(ws + L.vpart, nb, grad);
     *grad_out = grad;
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;

@@ -273,6 +273,7 @@ constexpr int IFACE_MIN_BLOCKS = FSL_IFACE_LANES == 4 ? 3 : 3;
 
 template <int S, int COLL, int L>
 __global__ void __launch_bounds__(LIST_BLOCK, IFACE_MIN_BLOCKS) k_curv_iface_fast(Dev d) {
+    pdl_enter();
     using St = Store<S>;
     int cnt[1];
     block_counts<1>(d.counts, {d.cif}, cnt);
@@ -489,6 +490,7 @@ __global__ void __launch_bounds__(LIST_BLOCK, IFACE_MIN_BLOCKS) k_curv_iface_fas
 
 template <int S, int COLL>
 __global__ void __launch_bounds__(LIST_BLOCK) k_curv_iface_slow(Dev d) {
+    pdl_enter();
     int cnt[1];
     block_counts<1>(d.counts, {C_SLOW}, cnt);
     const int n = cnt[0];
@@ -518,13 +520,17 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_curv_iface_slow(Dev d) {
 //     neighbours and m = 0; cells from liquid keep f and get m = rho;
 //  D  the excess mass (m - rho of a filled cell, m of an emptied one) is
 //     divided equally among the neighbours that are interface after B; the
-//     receivers gather it in k_fin_a.  No receiver: added to `lost`.
+//     receivers are marked (rmark) and gather it in k_fin_a.  No receiver:
+//     added to `lost`.
 // One block of 1024 threads with block barriers between the phases: a step
 // converts few cells, and one block keeps every phase visible to the next.
+// C and D touch disjoint cells (C the new interface cells, D the converted
+// ones) and read nothing the other writes, so they share one phase.
 constexpr int CONV_BLOCK = 1024;
 
 template <int S>
 __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
+    pdl_enter();
     using St = Store<S>;
     const int nfill = __ldcg(d.counts + C_FILL), nempty = __ldcg(d.counts + C_EMPTY);
     if (nfill + nempty == 0) return;
@@ -573,9 +579,35 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
         }
     }
     __syncthreads();
-    // C: new cells; lane q (1..18) reads neighbour x + c_q
+    // C (new cells; lane q (1..18) reads neighbour x + c_q) and D (excess of
+    // the converted cells) in one phase: item k < ngas + nliq is a new cell,
+    // the rest the converted cells
     const int ngas = __ldcg(d.counts + C_NEWGAS), nliq = __ldcg(d.counts + C_LIQ2IF);
-    for (int k = warp; k < ngas + nliq; k += nwarps) {
+    for (int k = warp; k < ngas + nliq + nfill + nempty; k += nwarps) {
+        if (k >= ngas + nliq) {
+            const int kc = k - ngas - nliq;
+            const bool isfill = kc < nfill;
+            const int i = isfill ? d.fill[kc] : d.empty[kc - nfill];
+            if (!isfill && !(__ldcg(d.flags + i) & B_TOGAS)) continue;  // warp-uniform
+            int x, y, z;
+            cell_coords(d, i, x, y, z);
+            bool recv = false;
+            if (act) {
+                const int j = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
+                const uint8_t fj = __ldcg(d.flags + j);
+                recv = ((fj & T_IF) && !(fj & (B_TOLIQ | B_TOGAS))) || (fj & B_NEW);
+                if (recv) d.rmark[j] = 1;
+            }
+            const int n = __popc(__ballot_sync(0xffffffffu, recv));
+            if (lane == 0) {
+                const float m = __ldcg(d.mass + i), r = __ldcg(d.rho + i);
+                const float mex = isfill ? m - r : m;
+                d.mass[i] = isfill ? r : 0.f;
+                d.excess[i] = n ? mex / n : 0.f;
+                if (n == 0) atomicAdd(d.lost, (double)mex);
+            }
+            continue;
+        }
         if (k < ngas) {
             const int j = d.newgas[k];
             int x, y, z;
@@ -629,35 +661,15 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
             }
         }
     }
-    __syncthreads();
-    // D
-    for (int k = warp; k < nfill + nempty; k += nwarps) {
-        const bool isfill = k < nfill;
-        const int i = isfill ? d.fill[k] : d.empty[k - nfill];
-        if (!isfill && !(__ldcg(d.flags + i) & B_TOGAS)) continue;  // warp-uniform
-        int x, y, z;
-        cell_coords(d, i, x, y, z);
-        bool recv = false;
-        if (act) {
-            const uint8_t fj = __ldcg(d.flags + nbr_index(d, x, y, z, cx(q), cy(q), cz(q)));
-            recv = ((fj & T_IF) && !(fj & (B_TOLIQ | B_TOGAS))) || (fj & B_NEW);
-        }
-        const int n = __popc(__ballot_sync(0xffffffffu, recv));
-        if (lane == 0) {
-            const float m = __ldcg(d.mass + i), r = __ldcg(d.rho + i);
-            const float mex = isfill ? m - r : m;
-            d.mass[i] = isfill ? r : 0.f;
-            d.excess[i] = n ? mex / n : 0.f;
-            if (n == 0) atomicAdd(d.lost, (double)mex);
-        }
-    }
 }
 
 // ---- final update ------------------------------------------------------------
 // A: cells that are interface at t+1 (old interface cells that did not convert,
-//    and the new ones) gather the excess mass of converted neighbours in fixed
-//    q order, set phi = m / rho and form the interface list of t+1.
+//    and the new ones) set phi = m / rho and form the interface list of t+1;
+//    those k_convert marked as receivers first gather the excess mass of their
+//    converted neighbours in fixed q order (and clear the mark).
 __global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
+    pdl_enter();
     int cnt[6];
     block_counts<6>(d.counts, {d.cif, C_NEWGAS, C_LIQ2IF, C_FILL, C_EMPTY, d.cdirty}, cnt);
     if (blockIdx.x == 0 && threadIdx.x == 0 && cnt[5]) d.counts[C_SEG] = 0;  // filled again by k_fin_b
@@ -671,7 +683,8 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
             const uint8_t fl = d.flags[i];
             if (!(k < nold && (fl & (B_TOLIQ | B_TOGAS)))) {
                 float m = d.mass[i];
-                if (any) {
+                if (any && d.rmark[i]) {  // a converted neighbour shares its excess with this cell
+                    d.rmark[i] = 0;
                     int x, y, z;
                     cell_coords(d, i, x, y, z);
                     for (int q = 1; q < Q; ++q) {
@@ -692,6 +705,7 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
 // list of active segments for the next step (block-aggregated compaction),
 // rebuilt only when a segment was switched on or off during the step
 __global__ void __launch_bounds__(256) k_fin_b(Dev d) {
+    pdl_enter();
     int cnt[5];
     block_counts<5>(d.counts, {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF, d.cdirty}, cnt);
     const int nfill = cnt[0], nempty = cnt[1], ngas = cnt[2], nliq = cnt[3];
@@ -777,8 +791,8 @@ template <int S, int COLL>
 void launch_ci(const Dev &d, cudaStream_t s) {
     static const int gf = list_blocks((const void *)k_curv_iface_fast<S, COLL, FSL_IFACE_LANES>, LIST_BLOCK, 4);
     static const int gs = list_blocks((const void *)k_curv_iface_slow<S, COLL>, LIST_BLOCK, 1);
-    k_curv_iface_fast<S, COLL, FSL_IFACE_LANES><<<gf, LIST_BLOCK, 0, s>>>(d);
-    k_curv_iface_slow<S, COLL><<<gs, LIST_BLOCK, 0, s>>>(d);
+    launch_pdl(k_curv_iface_fast<S, COLL, FSL_IFACE_LANES>, gf, LIST_BLOCK, s, d);
+    launch_pdl(k_curv_iface_slow<S, COLL>, gs, LIST_BLOCK, s, d);
 }
 
 void launch_sc_bulk(const Dev &d, cudaStream_t s) { FSL_DISPATCH(launch_bulk); }
@@ -802,8 +816,8 @@ void launch_convert(const Dev &d, cudaStream_t s) {
 void launch_finalize(const Dev &d, cudaStream_t s) {
     static const int ga = list_blocks((const void *)k_fin_a, LIST_BLOCK, 4);
     static const int gb = list_blocks((const void *)k_fin_b, 256, 4);
-    k_fin_a<<<ga, LIST_BLOCK, 0, s>>>(d);
-    k_fin_b<<<gb, 256, 0, s>>>(d);
+    launch_pdl(k_fin_a, ga, LIST_BLOCK, s, d);
+    launch_pdl(k_fin_b, gb, 256, s, d);
 }
 
 }  // namespace fslk
