@@ -265,14 +265,15 @@ def run_reference(args):
 PHASES = ["normals_plic", "lsqr_curvature", "sc_liquid", "sc_interface", "convert", "finalize"]
 
 
-def algorithmic_bytes(n_fluid, n_if, n_seg_cells, fused=False):
+def algorithmic_bytes(n_fluid, n_if, n_seg_cells, fused=False, pdf_bytes=4):
     """Bytes each phase must move at least, per launch (roofline table).
     fused: the LSQR curvature and the interface stream-collide run as one pass
-    (phase lsqr_curvature), the sc_interface phase is empty."""
+    (phase lsqr_curvature), the sc_interface phase is empty.  pdf_bytes: 4 for
+    FP32 PDFs, 2 for the 16-bit offset forms."""
     nb = {"normals_plic": 21.0 * n_if,           # phi + flag read, normal + offset written
           "lsqr_curvature": 21.0 * n_if,         # normal + flag read, kappa written
-          "sc_liquid": 152.0 * (n_fluid - n_if) + 1.0 * n_seg_cells,  # 19 PDFs in + 19 out, flags
-          "sc_interface": 248.0 * n_if,          # own + pulled + written PDFs, m, phi, kappa, rho
+          "sc_liquid": 38.0 * pdf_bytes * (n_fluid - n_if) + 1.0 * n_seg_cells,  # 19 PDFs in + 19 out, flags
+          "sc_interface": (57.0 * pdf_bytes + 20.0) * n_if,  # own + pulled + written PDFs, m, phi, kappa, rho, flag
           "convert": 0.0, "finalize": 14.0 * n_if}
     if fused:
         nb["lsqr_curvature"] += nb["sc_interface"]
@@ -345,9 +346,7 @@ def side_workload(F, S, name, storage, steps, stream, flush, peaks, seed):
     m1, l1 = sim.mass_total()
     ph = phase_profile(sim, min(steps, 20), flush)
     nseg_cells = n_fluid  # liquid rows are dense in this workload
-    nb = algorithmic_bytes(n_fluid, n_if, nseg_cells, fused=True)
-    if storage != "f32":
-        nb["sc_liquid"] = 76.0 * (n_fluid - n_if) + 1.0 * nseg_cells
+    nb = algorithmic_bytes(n_fluid, n_if, nseg_cells, fused=True, pdf_bytes=4 if storage == "f32" else 2)
     out = {"workload": name, "storage": storage, "fluid_cells": n_fluid, "interface_cells": n_if,
            "mlups": n_fluid * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
            "mass_drift_rel": ((m1 + l1) - (m0 + l0)) / (m0 + l0), "mass_drift_steps": steps,
@@ -670,7 +669,7 @@ def run_fsl(args):
                        "fsl_mass read back"}
 
     fused = args.curv == "lsqr"
-    nb = algorithmic_bytes(n_fluid, n_if, n_fluid, fused=fused)
+    nb = algorithmic_bytes(n_fluid, n_if, n_fluid, fused=fused, pdf_bytes=4 if args.storage == "f32" else 2)
     roof = roofline_of(ph, nb, peaks, workload=args.workload if args.storage == "f32" else None, fused=fused)
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -286,6 +286,43 @@ def test_single_step_parity_reduced_precision(orc, fsl, storage, tol_f):
     sim.close()
 
 
+@pytest.mark.parametrize("storage,tol_f", [(1, 1e-5), (2, 6e-5)])
+@pytest.mark.parametrize("nx", [70, 71])
+def test_reduced_precision_pool_spans_and_x_wrap(orc, fsl, storage, tol_f, nx):
+    """16-bit storage on a wavy pool between two walls that fills the whole x
+    range: liquid cells at x = 0 and x = nx - 1 pull across the periodic x
+    boundary, and the x rows end in a partial 32-cell segment (6 or 7 cells).
+    One step against the oracle from the decoded stored state, tolerances as
+    above."""
+    import copy
+    shape = (16, 12, nx)
+    phi = orc.fill(orc.geom("pool", h0=8.3, amp=1.2, wavelength=nx / 2.0, sub=8), shape)
+    obs = S.obstacle_mask(shape, (0, 15))
+    P = orc.params(shape, sigma=5e-4, tau=0.7)
+    st = orc.init_state(P, phi, obs)
+    fluid = (st.flags & 3) > 0
+    assert fluid.reshape(16, -1, nx)[:, :, 0].any() and fluid.reshape(16, -1, nx)[:, :, nx - 1].any()
+    fe = np.array([orc.feq(q, 1.0, np.array([0.03, -0.02, 0.01])) for q in range(19)])
+    st.f[:, fluid] = fe[:, None] + S.pdf_noise(7, shape, 2e-4)[:, fluid]
+    st.f = st.f.astype(np.float32).astype(np.float64)
+    Fp = fsl.make_params(shape, collision=P.collision, tau=P.tau, sigma=P.sigma, theta=P.theta, storage=storage)
+    sim = fsl.Sim(Fp, phi0=st.phi.astype(np.float32))
+    sim.set_state(st.f, st.flags, st.mass, st.phi)
+    st_in = copy.copy(st)
+    st_in.f = sim.host_state()["f"]
+    assert _guard_band(orc, P, st_in) == 0
+    ref, _, _, _ = orc.step(P, st_in)
+    sim.step(1)
+    h = sim.host_state()
+    assert np.array_equal(h["flags"] & fsl.TYPE_MASK, ref.flags)
+    liquid = ref.flags == 1
+    assert np.max(np.abs(h["f"][:, liquid] - ref.f[:, liquid])) <= tol_f
+    fl = (ref.flags & 3) > 0
+    assert np.max(np.abs(h["f"][:, fl] - ref.f[:, fl])) <= tol_f
+    assert sim.status() == 0
+    sim.close()
+
+
 @pytest.mark.parametrize("storage", [1, 2])
 def test_reduced_precision_mass_drift_is_small(orc, fsl, storage):
     """Rounding of the stored offsets makes the total mass drift; over 50 steps of
