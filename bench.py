@@ -372,23 +372,21 @@ def learned_curvature(F, S, stream, flush, peaks, seed, n_train, epochs, steps, 
     gen_s = time.perf_counter() - t0
     net = F.Mlp(S.mlp_init_weights(seed + 2))
     B = 4096
-    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     gen = torch.Generator(device="cuda").manual_seed(seed)
+    losses = torch.zeros(n_train // B, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     nsteps = 0
     for ep in range(epochs):
         perm = torch.randperm(n_train, device="cuda", generator=gen)
         lr = 2e-3 * (0.5 ** ep)
-        for b in range(0, n_train - B + 1, B):
-            idx = perm[b:b + B]
-            net.train_step(X[idx], target[idx], lr, loss_out=loss)
-            nsteps += 1
+        nsteps += net.train_epoch(X, target, perm, B, lr, losses=losses)  # batch loop in the library
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     out["training"] = {"stencils": n_train, "sub_samples": 8, "noise": 1e-3, "stencils_per_s": n_train / gen_s,
                        "epochs": epochs, "batch": B, "steps": nsteps, "samples_per_s": nsteps * B / train_s,
-                       "final_batch_loss": float(loss.item()),
+                       "final_batch_loss": float(losses[-1].item()),
+                       "loop": "fsl_mlp_train_epoch (device gather + step kernels, one C-ABI call per epoch)",
                        "flops_per_sample": 3 * 2 * (128 * 128 * 2 + 128)}
     del X, target
     torch.cuda.empty_cache()

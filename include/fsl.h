@@ -264,6 +264,24 @@ int fsl_mlp_gradients(const void *params, const void *X, const float *target, in
 int fsl_mlp_train_step(void *params, float *master, float *m, float *v, const void *X, const float *target, int n,
                        float lr, int step, float *loss_dev, void *workspace, void *stream);
 
+/* Bytes of workspace fsl_mlp_train_epoch needs for batches of `batch` rows. */
+size_t fsl_mlp_epoch_workspace(int batch);
+
+/* One pass over a training set, the batch loop inside the library: for
+ * b = 0 .. n/batch - 1 (a ragged tail is left out) the rows
+ * perm[b*batch .. (b+1)*batch) of X ([n][128] BF16 rows, device, 16-byte
+ * aligned) and of target (n floats, device) are gathered on the device and the
+ * step of fsl_mlp_train_step is taken with step counter step0 + b + 1.  perm:
+ * n int64 row indices on the device (a permutation for one epoch; an index
+ * outside [0, n) gathers a zero row and target 0).  losses_dev: NULL or n/batch
+ * floats (device) receiving each batch's loss.  workspace:
+ * fsl_mlp_epoch_workspace(batch) bytes, 256-byte aligned.  FSL_EINVAL for
+ * NULL pointers, batch < 1, n < batch, step0 < 0, lr <= 0 or misaligned
+ * pointers.  Asynchronous. */
+int fsl_mlp_train_epoch(void *params, float *master, float *m, float *v, const void *X, const float *target,
+                        const int64_t *perm, int n, int batch, float lr, int step0, float *losses_dev,
+                        void *workspace, void *stream);
+
 /* Packed parameters from FP32 master weights (BF16 rounding).  Asynchronous. */
 int fsl_mlp_pack(const float *master, void *params, void *stream);
 

@@ -236,6 +236,21 @@ __global__ void __launch_bounds__(1024) k_mlp_loss(const float *y, const float *
     if (threadIdx.x == 0) loss[0] = (float)(red[0] / n);
 }
 
+// Batch rows perm[0 .. rows) of X ([n][128] BF16) and target into Xb, tb: one
+// thread per 16-byte piece of a row.  An index outside [0, n) gathers a zero
+// row and target 0.
+constexpr int ROW_PIECES = MK * 2 / 16;
+__global__ void __launch_bounds__(256) k_mlp_gather(const uint4 *X, const float *target, const int64_t *perm, int rows,
+                                                    int n, uint4 *Xb, float *tb) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)rows * ROW_PIECES) return;
+    const int r = (int)(t / ROW_PIECES), c = (int)(t % ROW_PIECES);
+    const long long src = perm[r];
+    const bool ok = src >= 0 && src < n;
+    Xb[(long long)r * ROW_PIECES + c] = ok ? X[src * ROW_PIECES + c] : make_uint4(0u, 0u, 0u, 0u);
+    if (c == 0) tb[r] = ok ? target[src] : 0.f;
+}
+
 // Adam on the FP32 master parameters; refreshes the packed BF16 weights and FP32 biases
 __global__ void __launch_bounds__(256) k_mlp_adam(uint8_t *params, float *master, float *m, float *v,
                                                   const float *grad, float lr, float bc1, float bc2) {
@@ -592,17 +607,56 @@ int fsl_mlp_gradients(const void *params, const void *X, const float *target, in
                                                                                                        : FSL_ECUDA;
 }
 
-int fsl_mlp_train_step(void *params, float *master, float *m, float *v, const void *X, const float *target, int n,
-                       float lr, int step, float *loss_dev, void *workspace, void *stream) {
-    if (!params || !master || !m || !v || !X || !target || !workspace || n <= 0 || step < 1 || !(lr > 0.f))
-        return FSL_EINVAL;
+// gradients, then Adam with bias correction for step `step` (counted from 1)
+static int train_step(void *params, float *master, float *m, float *v, const void *X, const float *target, int n,
+                      float lr, int step, float *loss_dev, void *workspace, cudaStream_t s) {
     float *g = nullptr;
-    cudaStream_t s = (cudaStream_t)stream;
     const int rc = mlp_grad(params, X, target, n, loss_dev, workspace, &g, s);
     if (rc != FSL_OK) return rc;
     const float bc1 = (float)(1.0 - pow(0.9, step)), bc2 = (float)(1.0 - pow(0.999, step));
     k_mlp_adam<<<(M_COUNT + 255) / 256, 256, 0, s>>>(static_cast<uint8_t *>(params), master, m, v, g, lr, bc1, bc2);
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
+}
+
+int fsl_mlp_train_step(void *params, float *master, float *m, float *v, const void *X, const float *target, int n,
+                       float lr, int step, float *loss_dev, void *workspace, void *stream) {
+    if (!params || !master || !m || !v || !X || !target || !workspace || n <= 0 || step < 1 || !(lr > 0.f))
+        return FSL_EINVAL;
+    return train_step(params, master, m, v, X, target, n, lr, step, loss_dev, workspace, (cudaStream_t)stream);
+}
+
+// epoch workspace: the gathered batch rows (BF16) and targets, then the training workspace
+static size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+static size_t epoch_rows_bytes(int batch) { return up256((size_t)batch * MK * sizeof(__nv_bfloat16)); }
+static size_t epoch_target_bytes(int batch) { return up256((size_t)batch * sizeof(float)); }
+
+size_t fsl_mlp_epoch_workspace(int batch) {
+    if (batch <= 0) return 0;
+    return epoch_rows_bytes(batch) + epoch_target_bytes(batch) + fsl_mlp_train_workspace(batch);
+}
+
+int fsl_mlp_train_epoch(void *params, float *master, float *m, float *v, const void *X, const float *target,
+                        const int64_t *perm, int n, int batch, float lr, int step0, float *losses_dev,
+                        void *workspace, void *stream) {
+    if (!params || !master || !m || !v || !X || !target || !perm || !workspace || batch < 1 || n < batch ||
+        step0 < 0 || !(lr > 0.f))
+        return FSL_EINVAL;
+    if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(workspace) % 256) return FSL_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = static_cast<char *>(workspace);
+    uint4 *Xb = reinterpret_cast<uint4 *>(ws);
+    float *tb = reinterpret_cast<float *>(ws + epoch_rows_bytes(batch));
+    void *tws = ws + epoch_rows_bytes(batch) + epoch_target_bytes(batch);
+    const int nb = n / batch;
+    const int gblocks = (int)(((long long)batch * ROW_PIECES + 255) / 256);
+    for (int b = 0; b < nb; ++b) {
+        k_mlp_gather<<<gblocks, 256, 0, s>>>(static_cast<const uint4 *>(X), target, perm + (long long)b * batch, batch,
+                                             n, Xb, tb);
+        const int rc = train_step(params, master, m, v, Xb, tb, batch, lr, step0 + b + 1,
+                                  losses_dev ? losses_dev + b : nullptr, tws, s);
+        if (rc != FSL_OK) return rc;
+    }
+    return FSL_OK;
 }
 
 int fsl_mlp_pack(const float *master, void *params, void *stream) {

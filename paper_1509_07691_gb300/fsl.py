@@ -77,6 +77,9 @@ _SIGNATURES = {
                           [ctypes.c_void_p] * 4),
     "fsl_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_int, ctypes.c_float, ctypes.c_int] +
                            [ctypes.c_void_p] * 3),
+    "fsl_mlp_epoch_workspace": (ctypes.c_size_t, [ctypes.c_int]),
+    "fsl_mlp_train_epoch": (ctypes.c_int, [ctypes.c_void_p] * 7 + [ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                                                    ctypes.c_int] + [ctypes.c_void_p] * 3),
     "fsl_mlp_pack": (ctypes.c_int, [ctypes.c_void_p] * 3),
     "fsl_mlp_attach": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     "fsl_adjoint_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int,
@@ -429,6 +432,23 @@ class Mlp:
         check(lib().fsl_mlp_train_step(_ptr(self.params), _ptr(self.master), _ptr(self.m), _ptr(self.v), _ptr(X),
                                        _ptr(target), n, float(lr), self.step, _ptr(loss_out),
                                        _ptr(self._workspace(n)), _stream_handle(self.stream)), "fsl_mlp_train_step")
+
+    def train_epoch(self, X, target, perm, batch, lr, losses=None):
+        """One pass over (X, target) in the order perm, `batch` rows per Adam
+        step, the batch loop inside the library; a ragged tail is left out.
+        losses: None or a device tensor of n // batch floats for the batch
+        losses.  Returns the number of steps taken."""
+        n = X.shape[0]
+        assert perm.dtype == torch.int64 and perm.is_contiguous() and perm.numel() == n
+        need = lib().fsl_mlp_epoch_workspace(int(batch))
+        if getattr(self, "_ews", None) is None or self._ews.numel() < need:
+            self._ews = torch.empty(need, dtype=torch.uint8, device=self.device)
+        check(lib().fsl_mlp_train_epoch(_ptr(self.params), _ptr(self.master), _ptr(self.m), _ptr(self.v), _ptr(X),
+                                        _ptr(target), _ptr(perm), n, int(batch), float(lr), self.step, _ptr(losses),
+                                        _ptr(self._ews), _stream_handle(self.stream)), "fsl_mlp_train_epoch")
+        nb = n // batch
+        self.step += nb
+        return nb
 
     def master_dict(self):
         a = self.master.cpu().numpy()

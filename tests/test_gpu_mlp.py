@@ -108,6 +108,31 @@ def test_gradients_and_adam_match_oracle(F, M):
         assert np.max(np.abs(mw[k].astype(np.float64).reshape(np.shape(ref[k])) - ref[k])) <= 2e-6, k
 
 
+def test_train_epoch_matches_the_batch_loop(F, M):
+    """fsl_mlp_train_epoch (device gather of each batch, the step's kernels
+    issued from the library) takes the same steps as a loop of
+    fsl_mlp_train_step over host-side gathers: parameters, Adam moments and
+    batch losses bit-identical; the ragged tail is left out."""
+    import torch
+    n, B = 3 * 4096 + 100, 4096
+    p = S.mlp_sample_params(77, n)
+    X, target = F.mlp_stencils(p, sub=4, noise=1e-3, noise_seed=3)
+    perm = torch.randperm(n, device="cuda", generator=torch.Generator(device="cuda").manual_seed(5))
+    a, b = F.Mlp(S.mlp_init_weights(21)), F.Mlp(S.mlp_init_weights(21))
+    la = torch.zeros(n // B, dtype=torch.float32, device="cuda")
+    lb = torch.zeros(n // B, dtype=torch.float32, device="cuda")
+    for k in range(n // B):
+        idx = perm[k * B:(k + 1) * B]
+        a.train_step(X[idx].contiguous(), target[idx].contiguous(), 1e-3, loss_out=la[k:k + 1])
+    assert b.train_epoch(X, target, perm, B, 1e-3, losses=lb) == n // B
+    torch.cuda.synchronize()
+    assert a.step == b.step == n // B
+    for ta, tb in ((a.master, b.master), (a.m, b.m), (a.v, b.v), (a.params, b.params), (la, lb)):
+        assert torch.equal(ta, tb)
+    assert float(lb[-1]) > 0.0
+    assert F.Mlp.status() == 0
+
+
 def _lsqr_kappa_on_stencils(orc, stencils):
     """Oracle LSQR curvature of the middle cell of each 5x5x5 stencil."""
     out = []
