@@ -58,3 +58,18 @@ def test_workspace_size_and_validation_without_gpu(libpath):
     # fsl_init rejects a null fields pointer before touching the device
     ctx = ctypes.c_void_p()
     assert fsl.lib().fsl_init(ctypes.byref(p), None, None, 0, None, 0, None, ctypes.byref(ctx)) == fsl.EINVAL
+    # the training epoch: workspace = gathered batch (256 B rows + targets) + the step's workspace;
+    # bad arguments are rejected before any device work (the pointers below are never dereferenced)
+    L = fsl.lib()
+    assert L.fsl_mlp_epoch_workspace(0) == 0
+    assert L.fsl_mlp_epoch_workspace(4096) >= L.fsl_mlp_train_workspace(4096) + 4096 * (256 + 4)
+    fake = [ctypes.c_void_p(1 << 20)] * 7
+    def epoch(n, batch, lr=1e-3, step0=0, ptrs=fake, ws=ctypes.c_void_p(1 << 20)):
+        return L.fsl_mlp_train_epoch(*ptrs, n, batch, lr, step0, None, ws, None)
+    assert epoch(100, 4096) == fsl.EINVAL                       # fewer rows than one batch
+    assert epoch(8192, 0) == fsl.EINVAL
+    assert epoch(8192, 4096, lr=0.0) == fsl.EINVAL
+    assert epoch(8192, 4096, step0=-1) == fsl.EINVAL
+    assert epoch(8192, 4096, ptrs=[None] + fake[1:]) == fsl.EINVAL
+    assert epoch(8192, 4096, ptrs=fake[:4] + [ctypes.c_void_p((1 << 20) + 8)] + fake[5:]) == fsl.EINVAL  # X misaligned
+    assert epoch(8192, 4096, ws=ctypes.c_void_p((1 << 20) + 64)) == fsl.EINVAL  # workspace misaligned
