@@ -18,9 +18,13 @@ Parity status of the oracle functions
   step                        pinned: rest state, uniform flow, shear-wave decay
                               rate, exact mass conservation, type invariants,
                               Laplace pressure of a droplet
-  conversion readings         parity unpinned beyond mass conservation and the
-                              type invariants (the paper cites, but does not
-                              state, the conversion rules)
+  conversion readings         pinned on flat-interface scenarios whose outcome
+                              follows from the readings by counting (thresholds,
+                              filling beats emptying, new cells from gas and
+                              from liquid, 13 equal excess shares, new cells at
+                              the fluid neighbours' equilibrium), plus mass
+                              conservation and the type invariants (the paper
+                              cites, but does not state, the conversion rules)
 """
 from __future__ import annotations
 

@@ -795,8 +795,9 @@ void orc_curvature(const orc_params *P, const uint8_t *flags, const double *phi,
  * of the adjoint windows; central differences of it give the FP64 reference
  * gradient).
  * Pinned: rest state, uniform flow, shear-wave decay, exact mass
- * conservation, invariants; the conversion readings are otherwise unpinned;
- * the frozen step equals the plain step where nothing converts. */
+ * conservation, invariants; the conversion readings on flat-interface
+ * scenarios whose outcome follows from them by counting; the frozen step
+ * equals the plain step where nothing converts. */
 void orc_step(const orc_params *P, const double *fin, double *fout, uint8_t *flags, double *mass, double *phi,
               const double *kappa, const double *normal4, double *rho, double *lost, long *counts) {
     long N = ncell(P);
