@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--mlp-epochs", type=int, default=2)
     ap.add_argument("--mlp-only", action="store_true",
                     help="run only the MLP training section (no in-step inference) and print it")
+    ap.add_argument("--physics", action="store_true",
+                    help="run only the configuration reports (Laplace test, sessile caps, oscillation period)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint-window section (one evaluation, no checks) and print it")
     return ap.parse_args()
@@ -566,6 +568,106 @@ def adjoint_reference(window=50):
             "method": "central differences of the FP64 oracle window (frozen types), own target"}
 
 
+def _fill_weight(F, sim):
+    """Liquid fraction per cell: 1 in liquid, phi in interface, 0 elsewhere (device tensor)."""
+    import torch
+    fl = sim.flags_current() & F.TYPE_MASK
+    one = torch.ones_like(sim.phi)
+    return torch.where(fl == F.LIQUID, one, torch.where(fl == F.INTERFACE, sim.phi, torch.zeros_like(one)))
+
+
+def physics_reports(F, S, stream):
+    """The quantities the workload configurations ask to report, measured on the
+    GPU path with plain torch reductions of the state (diagnostics, not the hot
+    path):
+      droplet32 (200 steps, LSQR and FD): max spurious |u| over fluid cells and
+        the Laplace pressure (rho_in - rho_gas)/3 against 2 sigma/R, R from the
+        liquid volume;
+      sessile128 (5000 steps, theta = 30, 60, 90, 120 deg): apex height of the
+        cap against the spherical cap of the conserved volume at that angle;
+      oscillating256 (24000 steps): mode-2 period from the zero crossings of the
+        quadrupole moment against Rayleigh's inviscid value and Lamb's damped one."""
+    import torch
+    out = {}
+    # -- Laplace test
+    lap = {}
+    for curv in ("lsqr", "fd"):
+        w = S.workload("droplet32")
+        P, sim, phi0, obs = make_sim(F, w, curv, "f32", stream)
+        sim.step(w["steps"])
+        f = sim.pdfs_float()
+        c = torch.tensor([[0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0],
+                          [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1],
+                          [0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1]],
+                         dtype=torch.float32, device="cuda")
+        rho = f.sum(0)
+        u = torch.einsum("dq,qzyx->dzyx", c, f) / rho
+        fl = sim.flags_current() & F.TYPE_MASK
+        fluid = (fl == F.LIQUID) | (fl == F.INTERFACE)
+        umax = float(torch.sqrt((u * u).sum(0))[fluid].max())
+        wgt = _fill_weight(F, sim)
+        R = (3.0 * float(wgt.sum()) / (4.0 * math.pi)) ** (1.0 / 3.0)
+        g = w["geometry"]["c"]
+        zz, yy, xx = torch.meshgrid(*[torch.arange(n, device="cuda", dtype=torch.float32) for n in w["shape"]],
+                                    indexing="ij")
+        r = torch.sqrt((xx + 0.5 - g[0]) ** 2 + (yy + 0.5 - g[1]) ** 2 + (zz + 0.5 - g[2]) ** 2)
+        core = (fl == F.LIQUID) & (r < 0.5 * R)
+        dp = (float(rho[core].mean()) - 3.0 * P.p_gas) / 3.0
+        lap[curv] = {"max_u": umax, "dp": dp, "dp_laplace": 2.0 * w["sigma"] / R, "R_volume": R,
+                     "dp_rel_err": abs(dp - 2.0 * w["sigma"] / R) / (2.0 * w["sigma"] / R)}
+        sim.close()
+    out["laplace_droplet32"] = lap
+    # -- sessile caps
+    caps = {}
+    for th in (30.0, 60.0, 90.0, 120.0):
+        w = S.workload("sessile128", theta_deg=th)
+        P, sim, phi0, obs = make_sim(F, w, "lsqr", "f32", stream)
+        vol0 = float(_fill_weight(F, sim).sum())
+        sim.step(w["steps"])
+        wgt = _fill_weight(F, sim)
+        vol = float(wgt.sum())
+        h = float(wgt.sum(0).max())  # apex column: cells above the wall layer z = 0
+        ct = math.cos(math.radians(th))
+        Rc = (3.0 * vol / (math.pi * (1.0 - ct) ** 2 * (2.0 + ct))) ** (1.0 / 3.0)
+        h_cap = Rc * (1.0 - ct)
+        caps[f"{th:g}"] = {"height": h, "height_cap": h_cap, "rel_err": abs(h - h_cap) / h_cap,
+                           "volume": vol, "volume_drift_rel": (vol - vol0) / vol0, "steps": w["steps"]}
+        sim.close()
+    out["sessile128_caps"] = caps
+    # -- oscillation period
+    w = S.workload("oscillating256")
+    P, sim, phi0, obs = make_sim(F, w, "lsqr", "f32", stream)
+    zz, yy, xx = torch.meshgrid(*[torch.arange(n, device="cuda", dtype=torch.float32) for n in w["shape"]],
+                                indexing="ij")
+    every, total = 200, 24000
+    a = []
+    for k in range(total // every + 1):
+        if k:
+            sim.step(every)
+        wgt = _fill_weight(F, sim)
+        m = wgt.sum()
+        cx, cy, cz = (wgt * xx).sum() / m, (wgt * yy).sum() / m, (wgt * zz).sum() / m
+        izz = (wgt * (zz - cz) ** 2).sum() / m
+        ixy = 0.5 * ((wgt * (xx - cx) ** 2).sum() + (wgt * (yy - cy) ** 2).sum()) / m
+        a.append(float(izz - ixy))
+    sim.close()
+    t = np.arange(len(a)) * every
+    a = np.array(a)
+    zc = [t[i] + every * a[i] / (a[i] - a[i + 1]) for i in range(len(a) - 1) if a[i] * a[i + 1] < 0]
+    R = w["geometry"]["R"]
+    nu = (w["tau"] - 0.5) / 3.0
+    w0 = math.sqrt(8.0 * w["sigma"] / R ** 3)  # l (l - 1) (l + 2) = 8 for l = 2, rho = 1
+    gam = 5.0 * nu / R ** 2                      # (l - 1)(2 l + 1) nu / R^2
+    per = {"zero_crossings": [float(v) for v in zc], "samples_every": every, "steps": total,
+           "period_rayleigh": 2.0 * math.pi / w0,
+           "period_lamb_damped": 2.0 * math.pi / math.sqrt(max(w0 * w0 - gam * gam, 1e-30))}
+    if len(zc) >= 2:
+        per["period"] = 2.0 * float(np.mean(np.diff(zc)))
+        per["rel_err_lamb"] = abs(per["period"] - per["period_lamb_damped"]) / per["period_lamb_damped"]
+    out["oscillating256_period"] = per
+    return out
+
+
 def reduce_over_ranks(ms, n_fluid, device):
     """Timed milliseconds (max over ranks) and fluid cells (sum over ranks) of
     the default process group; the values themselves on a single process."""
@@ -746,6 +848,13 @@ def main():
                                inference=False)
         lc.pop("heldout")
         print(json.dumps({"learned_curvature": lc}))
+        return
+    if args.physics:
+        import torch
+        from paper_1509_07691_gb300 import build, synthetic as S
+        build.build()
+        from paper_1509_07691_gb300 import fsl as F
+        print(json.dumps({"physics": physics_reports(F, S, torch.cuda.current_stream())}))
         return
     if args.adjoint_only:
         import torch
