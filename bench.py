@@ -576,6 +576,14 @@ def _fill_weight(F, sim):
     return torch.where(fl == F.LIQUID, one, torch.where(fl == F.INTERFACE, sim.phi, torch.zeros_like(one)))
 
 
+def zero_crossings(a, every):
+    """Times of the sign changes of samples a[k] taken at t = k * every, by
+    linear interpolation between the two samples around each change."""
+    a = np.asarray(a, dtype=np.float64)
+    t = np.arange(len(a)) * every
+    return [float(t[i] + every * a[i] / (a[i] - a[i + 1])) for i in range(len(a) - 1) if a[i] * a[i + 1] < 0]
+
+
 def physics_reports(F, S, stream):
     """The quantities the workload configurations ask to report, measured on the
     GPU path with plain torch reductions of the state (diagnostics, not the hot
@@ -651,9 +659,7 @@ def physics_reports(F, S, stream):
         ixy = 0.5 * ((wgt * (xx - cx) ** 2).sum() + (wgt * (yy - cy) ** 2).sum()) / m
         a.append(float(izz - ixy))
     sim.close()
-    t = np.arange(len(a)) * every
-    a = np.array(a)
-    zc = [t[i] + every * a[i] / (a[i] - a[i + 1]) for i in range(len(a) - 1) if a[i] * a[i + 1] < 0]
+    zc = zero_crossings(a, every)
     R = w["geometry"]["R"]
     nu = (w["tau"] - 0.5) / 3.0
     w0 = math.sqrt(8.0 * w["sigma"] / R ** 3)  # l (l - 1) (l + 2) = 8 for l = 2, rho = 1
