@@ -56,6 +56,7 @@ extern "C" {
 #define FSL_ETIMEOUT (-4)     /* a bounded device wait gave up */
 #define FSL_ENAN (-5)         /* non-finite value found in the state */
 #define FSL_EUNSUPPORTED (-6) /* option not available in this build */
+#define FSL_EIO (-7)          /* checkpoint file unreadable, unwritable or not matching the context */
 
 /* cell types (Sec. II: liquid, interface, gas cells; walls are obstacle cells) */
 #define FSL_LIQUID 1
@@ -144,6 +145,23 @@ int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *ph
  * active row segments.
  * Asynchronous. */
 int fsl_refresh(struct fsl_ctx *ctx);
+
+/* Checkpoint and resume (a service of this library; the paper has no
+ * counterpart).  fsl_save writes the state of the context after all work
+ * queued on its stream: a header (magic "FSLCKPT1", format version 1, nx, ny,
+ * nz, storage, storage_shift, the lost-mass counter, the context's
+ * fsl_params), then the current PDF buffer f[parity] (19 N values in the
+ * storage type, f[q N + i]), the cell types (N bytes, type bits only), mass
+ * and phi (N floats each).  fsl_load reads such a file into a context with
+ * the same nx, ny, nz, storage and storage_shift (FSL_EIO otherwise; the
+ * other parameters of the loading context apply from then on), writes the
+ * state into the current buffers, restores the lost-mass counter and
+ * rebuilds the near-obstacle bits, interface list and active segments (as
+ * fsl_refresh).  Both are synchronising and stage one field at a time in
+ * host memory they allocate and free.  FSL_EINVAL for NULL arguments,
+ * FSL_EIO for file errors. */
+int fsl_save(struct fsl_ctx *ctx, const char *path);
+int fsl_load(struct fsl_ctx *ctx, const char *path);
 
 /* Advance nsteps time steps (Sec. II): curvature kappa(t) of every interface
  * cell by params.curv_model; pull stream with Eq. (reconstruct) at gas links

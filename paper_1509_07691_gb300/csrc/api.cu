@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/fsl.h: parameter checks, workspace layout,
 // step sequencing and CUDA-graph replay.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -319,6 +320,39 @@ int window_setup(fsl_ctx *c, char *ws, const AdjLayout &A, int *n_out) {
     CK(cudaStreamSynchronize(c->stream));
     *n_out = *c->host_count;
     return FSL_OK;
+}
+
+// checkpoint file layout and staging (fsl_save / fsl_load)
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t nx, ny, nz, storage, storage_shift;
+    int32_t pad;
+    double lost;
+    fsl_params params;
+};
+
+size_t pdf_elem_bytes(int storage) { return storage == FSL_F32 ? 4 : 2; }
+
+// one device buffer <-> file through a host staging buffer; false on any error
+bool dev_to_file(FILE *fp, const void *dev, size_t bytes, cudaStream_t s) {
+    void *h = malloc(bytes ? bytes : 1);
+    if (!h) return false;
+    bool ok = cudaMemcpyAsync(h, dev, bytes, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+              cudaStreamSynchronize(s) == cudaSuccess && fwrite(h, 1, bytes, fp) == bytes;
+    free(h);
+    return ok;
+}
+
+bool file_to_dev(FILE *fp, void *dev, size_t bytes, cudaStream_t s) {
+    void *h = malloc(bytes ? bytes : 1);
+    if (!h) return false;
+    bool ok = fread(h, 1, bytes, fp) == bytes &&
+              cudaMemcpyAsync(dev, h, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+              cudaStreamSynchronize(s) == cudaSuccess;
+    free(h);
+    return ok;
 }
 
 }  // namespace
@@ -686,6 +720,67 @@ int fsl_status(fsl_ctx *c) {
     return st;
 }
 
+// ---- checkpoint / resume -------------------------------------------------------
+int fsl_save(fsl_ctx *c, const char *path) {
+    if (!c || !path) return FSL_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FSL_ECUDA;
+    const size_t N = (size_t)c->p.nx * c->p.ny * c->p.nz;
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "FSLCKPT1", 8);
+    h.version = 1;
+    h.nx = c->p.nx;
+    h.ny = c->p.ny;
+    h.nz = c->p.nz;
+    h.storage = c->p.storage;
+    h.storage_shift = c->p.storage_shift;
+    h.params = c->p;
+    if (cudaMemcpy(&h.lost, c->base.lost, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return FSL_ECUDA;
+    // cell types without the near-obstacle and transient bits
+    uint8_t *fl = static_cast<uint8_t *>(malloc(N ? N : 1));
+    if (!fl) return FSL_EIO;
+    if (cudaMemcpy(fl, c->fields.flags[0], N, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        free(fl);
+        return FSL_ECUDA;
+    }
+    for (size_t i = 0; i < N; ++i) fl[i] &= T_MASK;
+    FILE *fp = fopen(path, "wb");
+    if (!fp) {
+        free(fl);
+        return FSL_EIO;
+    }
+    bool ok = fwrite(&h, sizeof h, 1, fp) == 1;
+    ok = ok && dev_to_file(fp, c->fields.f[c->parity], (size_t)Q * N * pdf_elem_bytes(c->p.storage), c->stream);
+    ok = ok && fwrite(fl, 1, N, fp) == N;
+    ok = ok && dev_to_file(fp, c->fields.mass, N * sizeof(float), c->stream);
+    ok = ok && dev_to_file(fp, c->fields.phi, N * sizeof(float), c->stream);
+    free(fl);
+    if (fclose(fp) != 0) ok = false;
+    return ok ? FSL_OK : FSL_EIO;
+}
+
+int fsl_load(fsl_ctx *c, const char *path) {
+    if (!c || !path) return FSL_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FSL_ECUDA;
+    const size_t N = (size_t)c->p.nx * c->p.ny * c->p.nz;
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return FSL_EIO;
+    CkptHeader h;
+    bool ok = fread(&h, sizeof h, 1, fp) == 1 && memcmp(h.magic, "FSLCKPT1", 8) == 0 && h.version == 1 &&
+              h.nx == c->p.nx && h.ny == c->p.ny && h.nz == c->p.nz && h.storage == c->p.storage &&
+              h.storage_shift == c->p.storage_shift;
+    ok = ok && file_to_dev(fp, c->fields.f[c->parity], (size_t)Q * N * pdf_elem_bytes(c->p.storage), c->stream);
+    ok = ok && file_to_dev(fp, c->fields.flags[0], N, c->stream);
+    ok = ok && file_to_dev(fp, c->fields.mass, N * sizeof(float), c->stream);
+    ok = ok && file_to_dev(fp, c->fields.phi, N * sizeof(float), c->stream);
+    fclose(fp);
+    if (!ok) return FSL_EIO;
+    if (cudaMemcpy(c->base.lost, &h.lost, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return FSL_ECUDA;
+    const int rc = fsl_refresh(c);
+    if (rc != FSL_OK) return rc;
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? FSL_OK : FSL_ECUDA;
+}
+
 const char *fsl_strerror(int code) {
     switch (code) {
     case FSL_OK: return "ok";
@@ -695,6 +790,7 @@ const char *fsl_strerror(int code) {
     case FSL_ETIMEOUT: return "bounded device wait timed out";
     case FSL_ENAN: return "non-finite value in the state";
     case FSL_EUNSUPPORTED: return "unsupported option";
+    case FSL_EIO: return "checkpoint file error or mismatch";
     default: return "unknown error";
     }
 }

@@ -18,7 +18,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libfsl.so")
 
-OK, EINVAL, ECUDA, ECAPACITY, ETIMEOUT, ENAN, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ECUDA, ECAPACITY, ETIMEOUT, ENAN, EUNSUPPORTED, EIO = 0, -1, -2, -3, -4, -5, -6, -7
 LIQUID, INTERFACE, GAS, OBSTACLE, TYPE_MASK, NEAR_OBSTACLE = 1, 2, 4, 8, 15, 16
 BGK, TRT = 0, 1
 CURV_LSQR, CURV_FD, CURV_NONE, CURV_MLP = 0, 1, 2, 3
@@ -59,6 +59,8 @@ _SIGNATURES = {
     "fsl_init": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(Fields), ctypes.c_void_p, ctypes.c_int,
                                 ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "fsl_refresh": (ctypes.c_int, [ctypes.c_void_p]),
+    "fsl_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "fsl_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "fsl_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "fsl_curvature": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "fsl_mass": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -347,6 +349,16 @@ class Sim:
                                        int(max_interface), _ptr(jac), _ptr(cells), _ptr(kap), ctypes.byref(n)),
               "fsl_kappa_jacobian")
         return jac[: n.value], cells[: n.value], kap[: n.value]
+
+    def save(self, path: str):
+        """Checkpoint of the current state (PDFs, types, mass, fill level, lost
+        mass) to a file; synchronising."""
+        check(lib().fsl_save(self.ctx, os.fsencode(path)), "fsl_save")
+
+    def load(self, path: str):
+        """Resume from a checkpoint written by save() on a grid of the same size
+        and storage; the lists are rebuilt.  Synchronising."""
+        check(lib().fsl_load(self.ctx, os.fsencode(path)), "fsl_load")
 
     def snapshot(self) -> dict:
         """Device copy of the current state (PDFs, types, mass, fill level)."""

@@ -73,3 +73,7 @@ def test_workspace_size_and_validation_without_gpu(libpath):
     assert epoch(8192, 4096, ptrs=[None] + fake[1:]) == fsl.EINVAL
     assert epoch(8192, 4096, ptrs=fake[:4] + [ctypes.c_void_p((1 << 20) + 8)] + fake[5:]) == fsl.EINVAL  # X misaligned
     assert epoch(8192, 4096, ws=ctypes.c_void_p((1 << 20) + 64)) == fsl.EINVAL  # workspace misaligned
+    # checkpoints: a NULL context or path is rejected before any file or device access
+    assert L.fsl_save(None, b"x.fslckpt") == fsl.EINVAL
+    assert L.fsl_load(None, b"x.fslckpt") == fsl.EINVAL
+    assert L.fsl_strerror(fsl.EIO).decode().startswith("checkpoint")
