@@ -593,8 +593,11 @@ def physics_reports(F, S, stream):
         liquid volume;
       sessile128 (5000 steps, theta = 30, 60, 90, 120 deg): apex height of the
         cap against the spherical cap of the conserved volume at that angle;
-      oscillating256 (24000 steps): mode-2 period from the zero crossings of the
-        quadrupole moment against Rayleigh's inviscid value and Lamb's damped one."""
+      oscillating256 (36000 steps, about two periods): mode-2 period from the
+        zero crossings of the quadrupole moment against Rayleigh's inviscid
+        value and Lamb's damped one;
+      full256 (256^3, every cell liquid, at rest): the liquid stream-collide
+        alone against the copy bandwidth."""
     import torch
     out = {}
     # -- Laplace test
@@ -602,7 +605,9 @@ def physics_reports(F, S, stream):
     for curv in ("lsqr", "fd"):
         w = S.workload("droplet32")
         P, sim, phi0, obs = make_sim(F, w, curv, "f32", stream)
+        m0, l0 = sim.mass_total()
         sim.step(w["steps"])
+        m1, l1 = sim.mass_total()
         f = sim.pdfs_float()
         c = torch.tensor([[0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0],
                           [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1],
@@ -622,7 +627,8 @@ def physics_reports(F, S, stream):
         core = (fl == F.LIQUID) & (r < 0.5 * R)
         dp = (float(rho[core].mean()) - 3.0 * P.p_gas) / 3.0
         lap[curv] = {"max_u": umax, "dp": dp, "dp_laplace": 2.0 * w["sigma"] / R, "R_volume": R,
-                     "dp_rel_err": abs(dp - 2.0 * w["sigma"] / R) / (2.0 * w["sigma"] / R)}
+                     "dp_rel_err": abs(dp - 2.0 * w["sigma"] / R) / (2.0 * w["sigma"] / R),
+                     "mass_drift_rel": ((m1 + l1) - (m0 + l0)) / (m0 + l0), "steps": w["steps"]}
         sim.close()
     out["laplace_droplet32"] = lap
     # -- sessile caps
@@ -635,10 +641,12 @@ def physics_reports(F, S, stream):
         wgt = _fill_weight(F, sim)
         vol = float(wgt.sum())
         h = float(wgt.sum(0).max())  # apex column: cells above the wall layer z = 0
-        ct = math.cos(math.radians(th))
+        r_wet = math.sqrt(float(wgt[1].sum()) / math.pi)  # footprint in the first layer above the wall
+        ct, st_ = math.cos(math.radians(th)), math.sin(math.radians(th))
         Rc = (3.0 * vol / (math.pi * (1.0 - ct) ** 2 * (2.0 + ct))) ** (1.0 / 3.0)
-        h_cap = Rc * (1.0 - ct)
+        h_cap, r_cap = Rc * (1.0 - ct), Rc * st_
         caps[f"{th:g}"] = {"height": h, "height_cap": h_cap, "rel_err": abs(h - h_cap) / h_cap,
+                           "contact_radius": r_wet, "contact_radius_cap": r_cap,
                            "volume": vol, "volume_drift_rel": (vol - vol0) / vol0, "steps": w["steps"]}
         sim.close()
     out["sessile128_caps"] = caps
@@ -647,7 +655,7 @@ def physics_reports(F, S, stream):
     P, sim, phi0, obs = make_sim(F, w, "lsqr", "f32", stream)
     zz, yy, xx = torch.meshgrid(*[torch.arange(n, device="cuda", dtype=torch.float32) for n in w["shape"]],
                                 indexing="ij")
-    every, total = 200, 24000
+    every, total = 200, 36000
     a = []
     for k in range(total // every + 1):
         if k:
@@ -671,6 +679,18 @@ def physics_reports(F, S, stream):
         per["period"] = 2.0 * float(np.mean(np.diff(zc)))
         per["rel_err_lamb"] = abs(per["period"] - per["period_lamb_damped"]) / per["period_lamb_damped"]
     out["oscillating256_period"] = per
+    # -- all-liquid box: the liquid stream-collide alone
+    shape = (256, 256, 256)
+    P = F.make_params(shape, collision=F.BGK, tau=0.6)
+    sim = F.Sim(P, phi0=torch.ones(shape, dtype=torch.float32, device="cuda"), stream=stream)
+    sim.step(5)
+    ms = time_steps(sim, 50, stream, torch.empty(64 << 20, dtype=torch.float32, device="cuda"))
+    n = shape[0] * shape[1] * shape[2]
+    gbs = 152.0 * n / (ms / 50 * 1e-3) / 1e9
+    out["full256"] = {"ms_per_step": ms / 50, "mlups": n / (ms / 50 * 1e-3) / 1e6, "achieved_gbs": gbs,
+                      "bytes_per_cell": 152, "note": "at rest (f = w_q); the step is the liquid stream-collide plus "
+                                                     "the empty list kernels"}
+    sim.close()
     return out
 
 
