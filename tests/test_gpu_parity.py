@@ -257,38 +257,6 @@ def test_mass_conservation_on_gpu(orc, fsl):
     sim.close()
 
 
-def test_checkpoint_round_trip(orc, fsl, tmp_path):
-    """fsl_save / fsl_load: the loaded state is the saved one (PDFs, types, mass,
-    fill level, total and lost mass), stepping on from it repeats the steps
-    taken after the save, and a context of another size refuses the file."""
-    P, st = _developed_state(orc, 3)
-    sim = _gpu_from_state(fsl, P, st, 0)
-    sim.step(3)
-    h0 = sim.host_state()
-    m0, l0 = sim.mass_total()
-    path = str(tmp_path / "state.fslckpt")
-    sim.save(path)
-    sim.step(4)
-    h4 = sim.host_state()
-    sim.load(path)
-    h = sim.host_state()
-    for k in ("f", "mass", "phi"):
-        assert np.array_equal(h[k], h0[k]), k
-    assert np.array_equal(h["flags"] & fsl.TYPE_MASK, h0["flags"] & fsl.TYPE_MASK)
-    assert sim.mass_total() == (m0, l0)
-    sim.step(4)
-    h = sim.host_state()
-    assert np.array_equal(h["flags"] & fsl.TYPE_MASK, h4["flags"] & fsl.TYPE_MASK)
-    for k in ("f", "mass", "phi"):
-        assert np.max(np.abs(h[k] - h4[k])) <= 1e-6, k
-    assert sim.status() == 0
-    sim.close()
-    other = _gpu_from_state(fsl, *_developed_state(orc, 3, shape=(20, 20, 20)), 0)
-    with pytest.raises(fsl.FslError):
-        other.load(path)
-    other.close()
-
-
 @pytest.mark.parametrize("storage,tol_f", [(1, 1e-5), (2, 6e-5)])
 def test_single_step_parity_reduced_precision(orc, fsl, storage, tol_f):
     """PDFs stored as 16-bit offsets f - w_q scaled by 2^8 (FP16 or BF16), collide
@@ -372,3 +340,35 @@ def test_reduced_precision_mass_drift_is_small(orc, fsl, storage):
     assert abs((m1 + l1) - (m0 + l0)) < 50 * nfluid * ulp * 0.01 * 19
     assert sim.status() == 0
     sim.close()
+
+
+def test_checkpoint_round_trip(orc, fsl, tmp_path):
+    """fsl_save / fsl_load: the loaded state is the saved one (PDFs, types, mass,
+    fill level, total and lost mass), stepping on from it repeats the steps
+    taken after the save, and a context of another size refuses the file."""
+    P, st = _developed_state(orc, 3)
+    sim = _gpu_from_state(fsl, P, st, 0)
+    sim.step(3)
+    h0 = sim.host_state()
+    m0, l0 = sim.mass_total()
+    path = str(tmp_path / "state.fslckpt")
+    sim.save(path)
+    sim.step(4)
+    h4 = sim.host_state()
+    sim.load(path)
+    h = sim.host_state()
+    for k in ("f", "mass", "phi"):
+        assert np.array_equal(h[k], h0[k]), k
+    assert np.array_equal(h["flags"] & fsl.TYPE_MASK, h0["flags"] & fsl.TYPE_MASK)
+    assert sim.mass_total() == (m0, l0)
+    sim.step(4)
+    h = sim.host_state()
+    assert np.array_equal(h["flags"] & fsl.TYPE_MASK, h4["flags"] & fsl.TYPE_MASK)
+    for k in ("f", "mass", "phi"):
+        assert np.max(np.abs(h[k] - h4[k])) <= 1e-6, k
+    assert sim.status() == 0
+    sim.close()
+    other = _gpu_from_state(fsl, *_developed_state(orc, 3, shape=(20, 20, 20)), 0)
+    with pytest.raises(fsl.FslError):
+        other.load(path)
+    other.close()
