@@ -13,11 +13,20 @@ Parity status of the oracle functions
   ls_fit / kappa_from_coef    pinned: exact quadric point sets, closed-form
                               mean curvature of tilted quadrics
   curvature (LSQR, FD)        pinned: planes (kappa = 0), spheres (kappa R -> 1,
-                              second order for LSQR), cube symmetries, spherical
-                              caps at the wall (contact-angle sign)
+                              second order for LSQR), cube symmetries (also of
+                              a walled box with an interface in a concave
+                              edge), spherical caps at the wall (contact-angle
+                              sign, both models), the FD closed form
+                              kappa = -cos(theta_eq)/4 of a vertical plane on
+                              a wall
+  reflect_phi                 pinned: the paper's reflection formula evaluated
+                              by hand on axis walls, a 45-degree staircase and
+                              next to a concave edge (neighbour set, aperture
+                              ties, weights)
   step                        pinned: rest state, uniform flow, shear-wave decay
                               rate, exact mass conservation, type invariants,
-                              Laplace pressure of a droplet
+                              Laplace pressure of a droplet; corner rule link by
+                              link on a hand-built contact-line cell
   conversion readings         pinned on flat-interface scenarios whose outcome
                               follows from the readings by counting (thresholds,
                               filling beats emptying, new cells from gas and
