@@ -20,7 +20,10 @@
  *                  cz : 0  0  0  0  0  1 -1  0  0  0  0  1 -1 -1  1  1 -1 -1  1
  *                stored as float (FSL_F32), or as (f - w_q) * 2^storage_shift in
  *                IEEE half (FSL_F16_OFS) or bfloat16 (FSL_BF16_OFS).
- *                Between steps the current buffer holds post-collision values f'.
+ *                Between steps the current buffer holds post-collision values f'
+ *                at liquid and interface cells.  fsl_init writes w_q into every
+ *                cell of both buffers; a non-fluid cell keeps w_q or the last
+ *                value written while it was fluid, and no step reads it.
  *   flags        one byte per cell: bits 0..3 the cell type (one of the FSL_*
  *                type values below), bit 4 FSL_NEAR_OBSTACLE (set by the
  *                library: the cell has an obstacle D3Q19 neighbour), bits 5..7
@@ -135,7 +138,8 @@ int fsl_fill_geometry(const fsl_params *params, const fsl_geometry *geom, float 
  *   obstacle   N bytes, nonzero = obstacle cell, host or device, or FSL_NONE;
  * then types from phi (phi <= 0 gas, >= 1 liquid, else interface; every
  * liquid cell with a gas neighbour becomes interface), f = w_q, m = phi, and
- * the interface list.  fields->f[0] and flags[0] hold the state afterwards.
+ * the interface list.  fields->f[0] and flags[0] hold the state afterwards;
+ * fields->f[1] is a copy of fields->f[0].
  * Asynchronous on `stream` (a cudaStream_t, or NULL for the default stream). */
 int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *phi0, int phi0_where,
              const uint8_t *obstacle, int obstacle_where, void *stream, struct fsl_ctx **out);
@@ -157,9 +161,11 @@ int fsl_refresh(struct fsl_ctx *ctx);
  * other parameters of the loading context apply from then on), writes the
  * state into the current buffers, restores the lost-mass counter and
  * rebuilds the near-obstacle bits, interface list and active segments (as
- * fsl_refresh).  Both are synchronising and stage one field at a time in
- * host memory they allocate and free.  FSL_EINVAL for NULL arguments,
- * FSL_EIO for file errors. */
+ * fsl_refresh).  fsl_load reads and checks the whole file (header fields and
+ * exact length) in host memory before it writes any device buffer, so a
+ * failed load (FSL_EIO) leaves the context's state unchanged.  Both are
+ * synchronising and stage data in host memory they allocate and free.
+ * FSL_EINVAL for NULL arguments, FSL_EIO for file errors. */
 int fsl_save(struct fsl_ctx *ctx, const char *path);
 int fsl_load(struct fsl_ctx *ctx, const char *path);
 

@@ -345,16 +345,6 @@ bool dev_to_file(FILE *fp, const void *dev, size_t bytes, cudaStream_t s) {
     return ok;
 }
 
-bool file_to_dev(FILE *fp, void *dev, size_t bytes, cudaStream_t s) {
-    void *h = malloc(bytes ? bytes : 1);
-    if (!h) return false;
-    bool ok = fread(h, 1, bytes, fp) == bytes &&
-              cudaMemcpyAsync(dev, h, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-              cudaStreamSynchronize(s) == cudaSuccess;
-    free(h);
-    return ok;
-}
-
 }  // namespace
 
 extern "C" {
@@ -422,6 +412,10 @@ int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *ph
         d0.fdst = fields->f[0];
         launch_init_state(d0, fields->flags[1], s);
         launch_seg_compact(d0, s);
+        // the second buffer starts as a copy, so every cell of both buffers
+        // holds a defined value (w_q away from the fluid) from here on
+        const size_t fbytes = (size_t)Q * N * pdf_elem_bytes(c->p.storage);
+        if (cudaMemcpyAsync(fields->f[1], fields->f[0], fbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) break;
         if (cudaGetLastError() != cudaSuccess) break;
         c->parity = 0;
         rc = FSL_OK;
@@ -763,22 +757,39 @@ int fsl_load(fsl_ctx *c, const char *path) {
     if (!c || !path) return FSL_EINVAL;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FSL_ECUDA;
     const size_t N = (size_t)c->p.nx * c->p.ny * c->p.nz;
+    const size_t fbytes = (size_t)Q * N * pdf_elem_bytes(c->p.storage);
+    // the whole file is read and checked before any device buffer changes, so
+    // a failed load leaves the context's state as it was
+    const size_t body = fbytes + N + 2 * N * sizeof(float);
     FILE *fp = fopen(path, "rb");
     if (!fp) return FSL_EIO;
     CkptHeader h;
     bool ok = fread(&h, sizeof h, 1, fp) == 1 && memcmp(h.magic, "FSLCKPT1", 8) == 0 && h.version == 1 &&
               h.nx == c->p.nx && h.ny == c->p.ny && h.nz == c->p.nz && h.storage == c->p.storage &&
               h.storage_shift == c->p.storage_shift;
-    ok = ok && file_to_dev(fp, c->fields.f[c->parity], (size_t)Q * N * pdf_elem_bytes(c->p.storage), c->stream);
-    ok = ok && file_to_dev(fp, c->fields.flags[0], N, c->stream);
-    ok = ok && file_to_dev(fp, c->fields.mass, N * sizeof(float), c->stream);
-    ok = ok && file_to_dev(fp, c->fields.phi, N * sizeof(float), c->stream);
+    char *buf = ok ? static_cast<char *>(malloc(body ? body : 1)) : nullptr;
+    ok = ok && buf && fread(buf, 1, body, fp) == body && fgetc(fp) == EOF;  // exact length
     fclose(fp);
-    if (!ok) return FSL_EIO;
-    if (cudaMemcpy(c->base.lost, &h.lost, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return FSL_ECUDA;
+    if (!ok) {
+        free(buf);
+        return FSL_EIO;
+    }
+    cudaStream_t s = c->stream;
+    const char *src = buf;
+    bool cu = cudaMemcpyAsync(c->fields.f[c->parity], src, fbytes, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    src += fbytes;
+    cu = cu && cudaMemcpyAsync(c->fields.flags[0], src, N, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    src += N;
+    cu = cu && cudaMemcpyAsync(c->fields.mass, src, N * sizeof(float), cudaMemcpyHostToDevice, s) == cudaSuccess;
+    src += N * sizeof(float);
+    cu = cu && cudaMemcpyAsync(c->fields.phi, src, N * sizeof(float), cudaMemcpyHostToDevice, s) == cudaSuccess;
+    cu = cu && cudaMemcpyAsync(c->base.lost, &h.lost, sizeof(double), cudaMemcpyHostToDevice, s) == cudaSuccess;
+    cu = cu && cudaStreamSynchronize(s) == cudaSuccess;  // the staging buffer is freed below
+    free(buf);
+    if (!cu) return FSL_ECUDA;
     const int rc = fsl_refresh(c);
     if (rc != FSL_OK) return rc;
-    return cudaStreamSynchronize(c->stream) == cudaSuccess ? FSL_OK : FSL_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? FSL_OK : FSL_ECUDA;
 }
 
 const char *fsl_strerror(int code) {

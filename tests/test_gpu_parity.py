@@ -343,12 +343,15 @@ def test_reduced_precision_mass_drift_is_small(orc, fsl, storage):
 
 
 def test_checkpoint_round_trip(orc, fsl, tmp_path):
-    """fsl_save / fsl_load: the loaded state is the saved one (PDFs, types, mass,
-    fill level, total and lost mass), stepping on from it repeats the steps
-    taken after the save, and a context of another size refuses the file."""
+    """fsl_save / fsl_load: the loaded state is the saved one bit for bit (PDFs
+    of every cell, types, mass, fill level, total and lost mass), stepping on
+    from it repeats the steps taken after the save, a truncated file and a
+    context of another size are refused, and a refused load changes nothing."""
+    import torch
     P, st = _developed_state(orc, 3)
     sim = _gpu_from_state(fsl, P, st, 0)
     sim.step(3)
+    snap0 = sim.snapshot()
     h0 = sim.host_state()
     m0, l0 = sim.mass_total()
     path = str(tmp_path / "state.fslckpt")
@@ -356,16 +359,31 @@ def test_checkpoint_round_trip(orc, fsl, tmp_path):
     sim.step(4)
     h4 = sim.host_state()
     sim.load(path)
-    h = sim.host_state()
+    snap = sim.snapshot()
     for k in ("f", "mass", "phi"):
-        assert np.array_equal(h[k], h0[k]), k
+        assert torch.equal(snap[k].view(torch.uint8), snap0[k].view(torch.uint8)), k
+    h = sim.host_state()
     assert np.array_equal(h["flags"] & fsl.TYPE_MASK, h0["flags"] & fsl.TYPE_MASK)
     assert sim.mass_total() == (m0, l0)
     sim.step(4)
     h = sim.host_state()
     assert np.array_equal(h["flags"] & fsl.TYPE_MASK, h4["flags"] & fsl.TYPE_MASK)
-    for k in ("f", "mass", "phi"):
+    fl = (h4["flags"] & 3) > 0
+    assert np.max(np.abs(h["f"][:, fl] - h4["f"][:, fl])) <= 1e-6
+    for k in ("mass", "phi"):
         assert np.max(np.abs(h[k] - h4[k])) <= 1e-6, k
+    # a truncated checkpoint is refused before any buffer is written
+    with open(path, "rb") as fp:
+        raw = fp.read()
+    short = str(tmp_path / "short.fslckpt")
+    with open(short, "wb") as fp:
+        fp.write(raw[: len(raw) - 64])
+    before = sim.snapshot()
+    with pytest.raises(fsl.FslError):
+        sim.load(short)
+    after = sim.snapshot()
+    for k in ("f", "flags", "mass", "phi"):
+        assert torch.equal(after[k].view(torch.uint8), before[k].view(torch.uint8)), k
     assert sim.status() == 0
     sim.close()
     other = _gpu_from_state(fsl, *_developed_state(orc, 3, shape=(20, 20, 20)), 0)
