@@ -12,6 +12,12 @@ Parity status of the oracle functions
                               closed forms, round trip
   ls_fit / kappa_from_coef    pinned: exact quadric point sets, closed-form
                               mean curvature of tilted quadrics
+  tr_fan / tr_cell (TR)       pinned: exact sphere points give 1/R and plane
+                              points 0 whatever the fan, symmetric rings on
+                              quadrics give the mean curvature A + B, uneven
+                              rings need the area weights, sub-sampled spheres
+                              (magnitude of the paper's TR errors), cube
+                              symmetry
   curvature (LSQR, FD)        pinned: planes (kappa = 0), spheres (kappa R -> 1,
                               second order for LSQR), cube symmetries (also of
                               a walled box with an interface in a concave
@@ -107,6 +113,8 @@ def lib():
                 "orc_ls_fit": (ctypes.c_int, [ctypes.c_int, _D, _D, ctypes.c_int, _D, _D, _D, _I]),
                 "orc_kappa_from_coef": (ctypes.c_double, [_D]),
                 "orc_curvature": (None, [P, _U8, _D, _D, _D, ctypes.c_int, _L]),
+                "orc_tr_fan": (ctypes.c_double, [ctypes.c_int, _D, _D, _D, _I]),
+                "orc_tr_cell": (ctypes.c_double, [P, _U8, _D, ctypes.c_long]),
                 "orc_step": (None, [P, _D, _D, _U8, _D, _D, _D, _D, _D, _D, _L]),
                 "orc_fill_cell": (ctypes.c_double, [G, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
                 "orc_fill": (None, [G, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]),
@@ -250,6 +258,20 @@ def reflect_phi(P: Params, flags, phi):
     out = np.zeros_like(phi)
     lib().orc_reflect_phi(ctypes.byref(P), _u8(flags), _d(phi), _d(out))
     return out
+
+
+def tr_fan(u, v, h, key=None):
+    """TR mean curvature of a fan of points (u, v, h) in the centre's tangent frame."""
+    u, v, h = (_f64(np.asarray(a).ravel()) for a in (u, v, h))
+    key = np.arange(u.size, dtype=np.int32) if key is None else np.ascontiguousarray(key, dtype=np.int32)
+    return lib().orc_tr_fan(int(u.size), _d(u), _d(v), _d(h), key.ctypes.data_as(_I))
+
+
+def tr_cell(P: Params, flags, normal4, i):
+    """TR curvature of cell index i from given normals and PLIC offsets (normal4[..., 4])."""
+    flags = np.ascontiguousarray(flags, np.uint8)
+    n4 = _f64(normal4)
+    return lib().orc_tr_cell(ctypes.byref(P), _u8(flags), _d(n4), int(i))
 
 
 def curvature(P: Params, flags, phi, iters=60):

@@ -42,7 +42,8 @@ static const int CZQ[NQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -
 typedef struct {
     int nx, ny, nz;
     int collision;   /* 0 = BGK, 1 = TRT (Sec. II) */
-    int curv_model;  /* 0 = LSQR (Sec. II.C), 1 = FD (Sec. II.A), 2 = none (kappa = 0) */
+    int curv_model;  /* 0 = LSQR (Sec. II.C), 1 = FD (Sec. II.A), 2 = none (kappa = 0),
+                        4 = TR (Sec. II.B) */
     int literal_phi; /* 1 = update phi by Eq. (advection1) literally instead of tracking mass */
     double tau;      /* relaxation time, nu = (tau - 1/2)/3 */
     double magic;    /* TRT parameter Lambda = (tau_e - 1/2)(tau_o - 1/2) */
@@ -642,6 +643,110 @@ static double lsqr_cell(const orc_params *P, const uint8_t *flags, const double 
 }
 
 /* ------------------------------------------------------------------------ */
+/* TR curvature (Sec. II.B, triangle fan of PLIC points after Pohl, curvature */
+/* after Taubin)                                                             */
+
+/* Mean curvature at the origin of a fan of m points given in the tangent
+ * frame of the centre point (u, v along the tangent plane, h along the
+ * centre normal, which points towards the liquid).  Readings of the two cited
+ * steps, which the paper does not spell out:
+ *  - fan: the points ordered by their angle atan2(v, u) around the normal
+ *    (ties by the index key[]), consecutive points joined with the centre
+ *    into triangles, cyclically; a pair whose angular gap is >= pi is not
+ *    joined (the fan is open there); points whose projection lies within
+ *    1e-6 of the centre are dropped;
+ *  - curvature: the normal curvature along each edge, kappa_j = 2 h_j /
+ *    |p_j|^2 (the circle through the centre, tangent to its plane, that
+ *    passes through p_j), averaged with weights equal to the summed areas of
+ *    the fan triangles that hold edge j (Taubin's weights; the trace of his
+ *    curvature tensor is this mean).
+ * Returns 0 if no triangle is formed.  Pinned: exact sphere and plane point
+ * sets, symmetric rings on quadrics (mean curvature A + B), uneven rings. */
+double orc_tr_fan(int m, const double *u, const double *v, const double *h, const int *key) {
+    double ang[27], kap[27], pu[27], pv[27], ph[27];
+    int kk[27], n = 0;
+    for (int j = 0; j < m && n < 27; ++j) {
+        double r2 = u[j] * u[j] + v[j] * v[j];
+        if (r2 < 1e-12) continue;
+        /* insertion by (angle, key) */
+        double a = atan2(v[j], u[j]);
+        int pos = n;
+        while (pos > 0 && (ang[pos - 1] > a || (ang[pos - 1] == a && kk[pos - 1] > key[j]))) {
+            ang[pos] = ang[pos - 1];
+            kap[pos] = kap[pos - 1];
+            pu[pos] = pu[pos - 1];
+            pv[pos] = pv[pos - 1];
+            ph[pos] = ph[pos - 1];
+            kk[pos] = kk[pos - 1];
+            --pos;
+        }
+        ang[pos] = a;
+        kap[pos] = 2.0 * h[j] / (r2 + h[j] * h[j]);
+        pu[pos] = u[j];
+        pv[pos] = v[j];
+        ph[pos] = h[j];
+        kk[pos] = key[j];
+        ++n;
+    }
+    if (n < 2) return 0.0;
+    const double pi = 3.14159265358979323846;
+    double num = 0, den = 0;
+    for (int k = 0; k < n; ++k) {
+        int s = (k + 1) % n;
+        double gap = ang[s] - ang[k];
+        if (s == 0) gap += 2.0 * pi;
+        if (gap >= pi) continue;
+        double a[3] = {pu[k], pv[k], ph[k]}, b[3] = {pu[s], pv[s], ph[s]}, c[3];
+        cross3(a, b, c);
+        double area = 0.5 * sqrt(dot3(c, c));
+        num += area * (kap[k] + kap[s]);
+        den += 2.0 * area;
+    }
+    return den > 0 ? num / den : 0.0;
+}
+
+/* TR curvature of interface cell i: the PLIC points p_j = x_j + a_j n_j of
+ * the other interface cells of the 3x3x3 block (nonzero normal; the same
+ * points as the LSQR fit, reading O20/O21) relative to the centre point,
+ * in the centre's frame (the LSQR frame rule), through orc_tr_fan with the
+ * block position (dz+1)*9 + (dy+1)*3 + (dx+1) as the tie key.  No wetting
+ * treatment (the paper leaves TR without one).  normal4 from orc_normals.
+ * Pinned: see orc_tr_fan; sub-sampled spheres; cube symmetry. */
+double orc_tr_cell(const orc_params *P, const uint8_t *flags, const double *normal4, long i) {
+    const double *ni = normal4 + 4 * i;
+    double n[3] = {ni[0], ni[1], ni[2]}, a = ni[3];
+    if (n[0] == 0 && n[1] == 0 && n[2] == 0) return 0.0;
+    int k = 0;
+    for (int j = 1; j < 3; ++j)
+        if (fabs(n[j]) < fabs(n[k])) k = j;
+    double e[3] = {0, 0, 0};
+    e[k] = 1;
+    double tu[3], tv[3];
+    cross3(e, n, tu);
+    unit(tu);
+    cross3(n, tu, tv);
+    double p[3] = {a * n[0], a * n[1], a * n[2]};
+    double u[27], v[27], h[27];
+    int key[27], m = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0 && dz == 0) continue;
+                long j = nbr(P, i, dx, dy, dz);
+                if (!(flags[j] & FL_IF)) continue;
+                const double *nj = normal4 + 4 * j;
+                if (nj[0] == 0 && nj[1] == 0 && nj[2] == 0) continue;
+                double d[3] = {dx + nj[3] * nj[0] - p[0], dy + nj[3] * nj[1] - p[1], dz + nj[3] * nj[2] - p[2]};
+                u[m] = dot3(d, tu);
+                v[m] = dot3(d, tv);
+                h[m] = dot3(d, n);
+                key[m] = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+                ++m;
+            }
+    return orc_tr_fan(m, u, v, h, key);
+}
+
+/* ------------------------------------------------------------------------ */
 /* FD curvature (Sec. II.A)                                                 */
 
 /* K8 kernel (1 - r^2/eps^2)^4 with eps = 2 on the 3x3x3 stencil, normalised
@@ -752,6 +857,10 @@ void orc_curvature(const orc_params *P, const uint8_t *flags, const double *phi,
     orc_normals(P, flags, phi, normal4, plic_iters);
     if (P->curv_model == 1) {
         fd_curvature(P, flags, phi, kappa);
+        return;
+    }
+    if (P->curv_model == 4) {
+        for (long i = 0; i < N; ++i) kappa[i] = (flags[i] & FL_IF) ? orc_tr_cell(P, flags, normal4, i) : 0.0;
         return;
     }
     for (long i = 0; i < N; ++i) {
