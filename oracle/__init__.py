@@ -33,6 +33,10 @@ Parity status of the oracle functions
                               rate, exact mass conservation, type invariants,
                               Laplace pressure of a droplet; corner rule link by
                               link on a hand-built contact-line cell
+  gas_volume / bubble_step    pinned: the volume of a sub-sampled bubble against
+                              4/3 pi R^3, p_g = p0 at V = V0, and Boyle's law
+                              for a bubble compressed by a liquid at higher
+                              pressure (the bubble shrinks until p_g matches it)
   conversion readings         pinned on flat-interface scenarios whose outcome
                               follows from the readings by counting (thresholds,
                               filling beats emptying, new cells from gas and
@@ -302,6 +306,24 @@ def step(P: Params, S: State, kappa=None, normal4=None, iters=60):
     out.f = fout
     out.lost = lost.value
     return out, counts, kappa, rho
+
+
+def gas_volume(S: State):
+    """Gas volume of a state (the bubble model of Sec. III.A): gas cells count
+    1, interface cells 1 - phi; liquid and obstacle cells 0."""
+    t = S.flags & 15
+    return float(np.count_nonzero(t == GAS) + np.sum(1.0 - S.phi[t == INTERFACE]))
+
+
+def bubble_step(P: Params, S: State, p0: float, V0: float, iters=60):
+    """One step with the bubble model (Sec. III.A): the gas pressure follows
+    the gas volume as an isothermal ideal gas, p_g = p0 V0 / V(t) (reading
+    B1), set from the state at t before the step; returns step()'s tuple and
+    the p_g used."""
+    import copy
+    Pb = copy.copy(P)
+    Pb.p_gas = p0 * V0 / gas_volume(S)
+    return step(Pb, S, iters=iters), Pb.p_gas
 
 
 def mass(P: Params, S: State):
