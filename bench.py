@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="fsl", choices=["fsl", "reference"])
     ap.add_argument("--workload", default="oscillating256")
-    ap.add_argument("--curv", default="lsqr", choices=["lsqr", "fd", "none"])
+    ap.add_argument("--curv", default="lsqr", choices=["lsqr", "fd", "none", "tr"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-side", action="store_true", help="skip the dense-pool and precision-form measurements")
@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--mlp-epochs", type=int, default=2)
     ap.add_argument("--mlp-only", action="store_true",
                     help="run only the MLP training section (no in-step inference) and print it")
+    ap.add_argument("--no-physics", action="store_true", help="skip the physics reports of the side sections")
     ap.add_argument("--physics", action="store_true",
                     help="run only the configuration reports (Laplace test, sessile caps, oscillation period)")
     ap.add_argument("--adjoint-only", action="store_true",
@@ -140,7 +141,7 @@ def geometry_kwargs(g: dict) -> dict:
 def make_sim(F, w, curv, storage, stream):
     import torch
     coll = F.TRT if w["collision"] == "trt" else F.BGK
-    cm = {"lsqr": F.CURV_LSQR, "fd": F.CURV_FD, "none": F.CURV_NONE}[curv]
+    cm = {"lsqr": F.CURV_LSQR, "fd": F.CURV_FD, "none": F.CURV_NONE, "tr": F.CURV_TR, "mlp": F.CURV_MLP}[curv]
     st = {"f32": F.F32, "f16": F.F16_OFS, "bf16": F.BF16_OFS}[storage]
     P = F.make_params(w["shape"], collision=coll, curv_model=cm, storage=st, tau=w["tau"], sigma=w["sigma"],
                       theta=w["theta"])
@@ -329,18 +330,25 @@ PHASES = ["normals_plic", "lsqr_curvature", "sc_liquid", "sc_interface", "conver
 
 
 def algorithmic_bytes(n_fluid, n_if, n_seg_cells, fused=False, pdf_bytes=4):
-    """Bytes each phase must move at least, per launch (roofline table).
-    fused: the LSQR curvature and the interface stream-collide run as one pass
-    (phase lsqr_curvature), the sc_interface phase is empty.  pdf_bytes: 4 for
-    FP32 PDFs, 2 for the 16-bit offset forms."""
+    """Bytes each phase must move at least, per launch.  Per interface cell:
+    normals 21 B (phi and flag read, normal and offset written), LSQR fit 21 B
+    (normal and flag read, kappa written), interface stream-collide 57 PDFs
+    (own 19 read, 18 pulled, 19 written) plus m, phi, kappa, rho and the flag
+    (20 B); per liquid cell 38 PDFs plus 1 B of flags per segment cell; the
+    final update 14 B per interface cell.  fused: the LSQR step's brick pass
+    (normals, fit and interface stream-collide in one kernel, phase
+    lsqr_curvature; the normals phase is the step prologue and the
+    sc_interface phase holds the deferred cells).  pdf_bytes: 4 for FP32
+    PDFs, 2 for the 16-bit offset forms."""
     nb = {"normals_plic": 21.0 * n_if,           # phi + flag read, normal + offset written
           "lsqr_curvature": 21.0 * n_if,         # normal + flag read, kappa written
           "sc_liquid": 38.0 * pdf_bytes * (n_fluid - n_if) + 1.0 * n_seg_cells,  # 19 PDFs in + 19 out, flags
           "sc_interface": (57.0 * pdf_bytes + 20.0) * n_if,  # own + pulled + written PDFs, m, phi, kappa, rho, flag
           "convert": 0.0, "finalize": 14.0 * n_if}
     if fused:
-        nb["lsqr_curvature"] += nb["sc_interface"]
+        nb["lsqr_curvature"] += nb["sc_interface"] + nb["normals_plic"]
         nb["sc_interface"] = 0.0
+        nb["normals_plic"] = 0.0
     return nb
 
 
@@ -385,7 +393,7 @@ def measured_traffic(kernel, workload):
 def roofline_of(ph, nbytes, peaks, which=None, workload=None, fused=False):
     k = which if which is not None else int(np.argmax(ph))
     name = PHASES[k]
-    label = "lsqr_curvature+sc_interface (fused)" if fused and name == "lsqr_curvature" else name
+    label = "k_brick: normals + LSQR + interface stream-collide (fused)" if fused and name == "lsqr_curvature" else name
     hbm = peaks.get("hbm_gbs", 6800.0)
     ach = nbytes[name] / (ph[k] * 1e-3) / 1e9
     return {"kernel": label, "bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": hbm, "frac": ach / hbm,
@@ -462,6 +470,7 @@ def learned_curvature(F, S, stream, flush, peaks, seed, n_train, epochs, steps, 
     Xt, tt = F.mlp_stencils(q, sub=8, noise=1e-3, noise_seed=seed + 5)
     yt = net.forward(Xt).cpu().numpy()
     out["heldout"] = {"params": q, "noise_seed": seed + 5, "truth": tt.cpu().numpy(), "mlp": yt}
+    out["net"] = net
     if not inference:
         return out
     # inference inside FSLBM
@@ -645,52 +654,202 @@ def zero_crossings(a, every):
     return [float(t[i] + every * a[i] / (a[i] - a[i + 1])) for i in range(len(a) - 1) if a[i] * a[i + 1] < 0]
 
 
-def physics_reports(F, S, stream):
+def _velocity(F, sim):
+    """(rho, u[3]) of the current PDFs (device tensors)."""
+    import torch
+    f = sim.pdfs_float()
+    c = torch.tensor([[0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0],
+                      [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1],
+                      [0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1]],
+                     dtype=torch.float32, device=f.device)
+    rho = f.sum(0)
+    return rho, torch.einsum("dq,qzyx->dzyx", c, f) / rho
+
+
+def laplace_report(F, S, stream, curv, storage, net=None):
+    """Static droplet (droplet32: 32^3, R = 8, sigma = 1e-4, tau = 1, 200
+    steps): max spurious |u| over the fluid cells, the Laplace pressure
+    (rho_core - 3 p_g)/3 against 2 sigma/R (R from the liquid volume, core =
+    liquid cells within R/2 of the centre), the curvature of the interface
+    cells against 1/R (mean of kappa R and its r.m.s. deviation from 1) and
+    the mass drift."""
+    import torch
+    w = S.workload("droplet32")
+    P, sim, phi0, obs = make_sim(F, w, curv, storage, stream)
+    if curv == "mlp":
+        sim.attach_mlp(net, 0.05)
+    m0, l0 = sim.mass_total()
+    sim.step(w["steps"])
+    m1, l1 = sim.mass_total()
+    rho, u = _velocity(F, sim)
+    fl = sim.flags_current() & F.TYPE_MASK
+    fluid = (fl == F.LIQUID) | (fl == F.INTERFACE)
+    umag = torch.sqrt((u * u).sum(0))[fluid]
+    wgt = _fill_weight(F, sim)
+    R = (3.0 * float(wgt.sum()) / (4.0 * math.pi)) ** (1.0 / 3.0)
+    g = w["geometry"]["c"]
+    zz, yy, xx = torch.meshgrid(*[torch.arange(n, device="cuda", dtype=torch.float32) for n in w["shape"]],
+                                indexing="ij")
+    r = torch.sqrt((xx - g[0]) ** 2 + (yy - g[1]) ** 2 + (zz - g[2]) ** 2)
+    core = (fl == F.LIQUID) & (r < 0.5 * R)
+    dp = (float(rho[core].mean()) - 3.0 * P.p_gas) / 3.0
+    kap = torch.empty_like(sim.kappa)
+    cm = {"lsqr": F.CURV_LSQR, "fd": F.CURV_FD, "tr": F.CURV_TR, "mlp": F.CURV_MLP}[curv]
+    sim.curvature(cm, kap)
+    kr = kap[fl == F.INTERFACE].double() * R
+    out = {"max_u": float(umag.max()), "mean_u": float(umag.mean()), "dp": dp, "dp_laplace": 2.0 * w["sigma"] / R,
+           "R_volume": R, "dp_rel_err": abs(dp - 2.0 * w["sigma"] / R) / (2.0 * w["sigma"] / R),
+           "kappa_R_mean": float(kr.mean()), "kappa_R_rms_err": float(torch.sqrt(((kr - 1.0) ** 2).mean())),
+           "mass_drift_rel": ((m1 + l1) - (m0 + l0)) / (m0 + l0), "steps": w["steps"], "storage": storage}
+    if curv == "mlp":
+        st = sim.stats()
+        out["mlp_kept_fraction"] = float(st[9]) / max(1, int(st[8]))
+    sim.close()
+    return out
+
+
+# Tab. advection as printed (percent): d -> (L1, L2) for convective and diffusive scaling
+ADVECTION_TABLE = {10: ((3.00, 9.38), (3.00, 9.38)), 20: ((1.63, 7.19), (1.38, 6.17)),
+                   40: ((1.25, 7.38), (0.85, 5.39)), 80: ((1.17, 8.44), (0.68, 5.87))}
+
+
+def advection_report(F, stream, diameters=(10, 20, 40, 80)):
+    """Tab. advection (Sec. III.A): a gas bubble of diameter d in a periodic
+    box of 2d cells carried by a prescribed constant flow (f = feq(1, u0)
+    before every step, fsl_prescribe_flow) for T = d/u0 steps; L1 and L2 of
+    the bubble indicator 1 - phi against the initial field shifted by d (the
+    domain-independent reading of the paper's norms).  Convective scaling:
+    u0 = 0.05; diffusive: u0 = 0.05 * 10 / d."""
+    import torch
+    out = {}
+    for d in diameters:
+        row = {}
+        for k, (name, u0) in enumerate((("convective", 0.05), ("diffusive", 0.05 * 10.0 / d))):
+            L = 2 * d
+            shape = (L, L, L)
+            P = F.make_params(shape, tau=1.0, sigma=0.0, curv_model=F.CURV_NONE)
+            phi0 = torch.zeros(shape, dtype=torch.float32, device="cuda")
+            F.fill_geometry(P, F.make_geometry("sphere", c=(L / 2, L / 2, L / 2), R=d / 2.0, invert=1, sub=16), phi0,
+                            stream)
+            sim = F.Sim(P, phi0=phi0, stream=stream)
+            g0 = 1.0 - sim.phi.double()
+            T = int(round(d / u0))
+            t0 = time.perf_counter()
+            for _ in range(T):
+                sim.prescribe_flow(1.0, (u0, 0.0, 0.0))
+                sim.step(1)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            g1 = 1.0 - torch.roll(sim.phi.double(), -d, dims=2)
+            l1 = float((g1 - g0).abs().sum() / g0.sum())
+            l2 = float(torch.sqrt(((g1 - g0) ** 2).sum() / (g0 ** 2).sum()))
+            p1, p2 = ADVECTION_TABLE.get(d, ((None, None), (None, None)))[k]
+            row[name] = {"u0": u0, "steps": T, "L1_pct": 100 * l1, "L2_pct": 100 * l2, "paper_L1_pct": p1,
+                         "paper_L2_pct": p2, "seconds": sec}
+            sim.close()
+        out[str(d)] = row
+    return out
+
+
+def renardy_bubble(F, stream, dx_inv, curv, steps, moving=False, sample_every=0):
+    """The Laplace test of Sec. III.A on a bubble (Renardy's setup): unit box,
+    R = 0.125, rho = 4, mu = 1, sigma = 0.357, gas pressure by the bubble
+    model.  Lattice units at dx = 1/dx_inv under the paper's time steps
+    (dt = 1e-4 (48/dx_inv)^2): nu = mu/rho dt/dx^2, tau = 3 nu + 1/2,
+    sigma_lb = sigma/rho dt^2/dx^3, R = dx_inv/8 cells.  Static frame: no-slip
+    walls at z = 0 and 1 (obstacle layers), periodic in x and y.  Moving frame
+    (moving=True): u0 = 0.0024 along x added to the liquid, periodic in all
+    directions (reading E2: a background flow with no-slip walls would be
+    sheared), run for T = L/u0 steps.  Reports the maximum spurious |u| (in
+    the moving frame |u - u0|) over fluid cells, in lattice units and in
+    units of the box per unit time (x dx/dt), and L2(kappa) = sqrt(sum
+    (kappa + 1/R)^2 / sum (1/R)^2) over the interface cells."""
+    import torch
+    L = dx_inv
+    dt = 1e-4 * (48.0 / dx_inv) ** 2
+    dx = 1.0 / dx_inv
+    nu = 0.25 * dt / dx ** 2
+    tau = 3.0 * nu + 0.5
+    sig = 0.357 / 4.0 * dt ** 2 / dx ** 3
+    R = L / 8.0
+    u0 = 0.0024 if moving else 0.0
+    if moving:
+        shape, walls = (L, L, L), None
+        c = (L / 2 + 0.13, L / 2 - 0.21, L / 2 + 0.07)
+    else:
+        shape = (L + 2, L, L)
+        walls = torch.zeros(shape, dtype=torch.uint8, device="cuda")
+        walls[0] = 1
+        walls[-1] = 1
+        c = (L / 2 + 0.13, L / 2 - 0.21, (L + 2) / 2 - 0.5 + 0.07)
+    cm = {"lsqr": F.CURV_LSQR, "fd": F.CURV_FD, "tr": F.CURV_TR}[curv]
+    P = F.make_params(shape, tau=tau, sigma=sig, curv_model=cm)
+    phi0 = torch.zeros(shape, dtype=torch.float32, device="cuda")
+    F.fill_geometry(P, F.make_geometry("sphere", c=c, R=R, invert=1, sub=16), phi0, stream)
+    if walls is not None:
+        phi0[walls > 0] = 0.0
+    sim = F.Sim(P, phi0=phi0, obstacle=walls, stream=stream)
+    if moving:
+        sim.prescribe_flow(1.0, (u0, 0.0, 0.0))  # initial liquid state: feq(1, u0)
+    sim.set_bubble(1.0 / 3.0)
+    hist = []
+
+    def l2k():
+        kap = torch.empty_like(sim.kappa)
+        sim.curvature(cm, kap)
+        fl = sim.flags_current() & F.TYPE_MASK
+        k = kap[fl == F.INTERFACE].double()
+        return float(torch.sqrt(((k + 1.0 / R) ** 2).sum() / (k.numel() / R ** 2)))
+
+    done = 0
+    t0 = time.perf_counter()
+    while done < steps:
+        n = min(steps - done, sample_every or steps)
+        sim.step(n)
+        done += n
+        if sample_every:
+            hist.append((done, l2k()))
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    rho, u = _velocity(F, sim)
+    fl = sim.flags_current() & F.TYPE_MASK
+    fluid = (fl == F.LIQUID) | (fl == F.INTERFACE)
+    u[0] -= u0
+    umag = torch.sqrt((u * u).sum(0))[fluid]
+    out = {"dx": dx, "dt": dt, "tau": tau, "sigma_lb": sig, "R_cells": R, "grid": list(shape[::-1]), "steps": steps,
+           "max_u_lb": float(umag.max()), "mean_u_lb": float(umag.mean()),
+           "max_u_box_units": float(umag.max()) * dx / dt, "L2_kappa": l2k(), "bubble": list(sim.bubble()),
+           "seconds": sec}
+    if hist:
+        out["L2_kappa_history"] = hist
+    sim.close()
+    return out
+
+
+def physics_reports(F, S, stream, net=None):
     """The quantities the workload configurations ask to report, measured on the
     GPU path with plain torch reductions of the state (diagnostics, not the hot
     path):
-      droplet32 (200 steps, LSQR and FD): max spurious |u| over fluid cells and
-        the Laplace pressure (rho_in - rho_gas)/3 against 2 sigma/R, R from the
-        liquid volume;
-      sessile128 (5000 steps, theta = 30, 60, 90, 120 deg): apex height of the
-        cap against the spherical cap of the conserved volume at that angle;
-      oscillating256 (36000 steps, about two periods): mode-2 period from the
-        zero crossings of the quadrupole moment against Rayleigh's inviscid
-        value and Lamb's damped one;
+      droplet32 (200 steps): laplace_report for the LSQR, FD and TR models in
+        FP32, LSQR with FP16 and BF16 offset storage, and the learned
+        curvature (LSQR judge) when a trained network is given;
+      sessile128 (5000 steps, theta = 30, 60, 90, 120 deg): apex height and
+        contact radius of the cap against the spherical cap of the conserved
+        volume at that angle;
+      oscillating256 (36000 steps, about two periods), FP32 and the FP16 and
+        BF16 offset forms: mode-2 period from the zero crossings of the
+        quadrupole moment against Rayleigh's inviscid value and Lamb's damped
+        one, and the mass drift;
       full256 (256^3, every cell liquid, at rest): the liquid stream-collide
         alone against the copy bandwidth."""
     import torch
     out = {}
-    # -- Laplace test
     lap = {}
-    for curv in ("lsqr", "fd"):
-        w = S.workload("droplet32")
-        P, sim, phi0, obs = make_sim(F, w, curv, "f32", stream)
-        m0, l0 = sim.mass_total()
-        sim.step(w["steps"])
-        m1, l1 = sim.mass_total()
-        f = sim.pdfs_float()
-        c = torch.tensor([[0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0],
-                          [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1],
-                          [0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1]],
-                         dtype=torch.float32, device="cuda")
-        rho = f.sum(0)
-        u = torch.einsum("dq,qzyx->dzyx", c, f) / rho
-        fl = sim.flags_current() & F.TYPE_MASK
-        fluid = (fl == F.LIQUID) | (fl == F.INTERFACE)
-        umax = float(torch.sqrt((u * u).sum(0))[fluid].max())
-        wgt = _fill_weight(F, sim)
-        R = (3.0 * float(wgt.sum()) / (4.0 * math.pi)) ** (1.0 / 3.0)
-        g = w["geometry"]["c"]
-        zz, yy, xx = torch.meshgrid(*[torch.arange(n, device="cuda", dtype=torch.float32) for n in w["shape"]],
-                                    indexing="ij")
-        r = torch.sqrt((xx + 0.5 - g[0]) ** 2 + (yy + 0.5 - g[1]) ** 2 + (zz + 0.5 - g[2]) ** 2)
-        core = (fl == F.LIQUID) & (r < 0.5 * R)
-        dp = (float(rho[core].mean()) - 3.0 * P.p_gas) / 3.0
-        lap[curv] = {"max_u": umax, "dp": dp, "dp_laplace": 2.0 * w["sigma"] / R, "R_volume": R,
-                     "dp_rel_err": abs(dp - 2.0 * w["sigma"] / R) / (2.0 * w["sigma"] / R),
-                     "mass_drift_rel": ((m1 + l1) - (m0 + l0)) / (m0 + l0), "steps": w["steps"]}
-        sim.close()
+    for key, curv, storage in (("lsqr", "lsqr", "f32"), ("fd", "fd", "f32"), ("tr", "tr", "f32"),
+                               ("lsqr_f16", "lsqr", "f16"), ("lsqr_bf16", "lsqr", "bf16")):
+        lap[key] = laplace_report(F, S, stream, curv, storage)
+    if net is not None:
+        lap["mlp"] = laplace_report(F, S, stream, "mlp", "f32", net)
     out["laplace_droplet32"] = lap
     # -- sessile caps
     caps = {}
@@ -708,38 +867,53 @@ def physics_reports(F, S, stream):
         h_cap, r_cap = Rc * (1.0 - ct), Rc * st_
         caps[f"{th:g}"] = {"height": h, "height_cap": h_cap, "rel_err": abs(h - h_cap) / h_cap,
                            "contact_radius": r_wet, "contact_radius_cap": r_cap,
+                           "contact_radius_rel_err": abs(r_wet - r_cap) / r_cap,
                            "volume": vol, "volume_drift_rel": (vol - vol0) / vol0, "steps": w["steps"]}
         sim.close()
     out["sessile128_caps"] = caps
-    # -- oscillation period
-    w = S.workload("oscillating256")
-    P, sim, phi0, obs = make_sim(F, w, "lsqr", "f32", stream)
-    zz, yy, xx = torch.meshgrid(*[torch.arange(n, device="cuda", dtype=torch.float32) for n in w["shape"]],
-                                indexing="ij")
-    every, total = 200, 36000
-    a = []
-    for k in range(total // every + 1):
-        if k:
-            sim.step(every)
-        wgt = _fill_weight(F, sim)
-        m = wgt.sum()
-        cx, cy, cz = (wgt * xx).sum() / m, (wgt * yy).sum() / m, (wgt * zz).sum() / m
-        izz = (wgt * (zz - cz) ** 2).sum() / m
-        ixy = 0.5 * ((wgt * (xx - cx) ** 2).sum() + (wgt * (yy - cy) ** 2).sum()) / m
-        a.append(float(izz - ixy))
-    sim.close()
-    zc = zero_crossings(a, every)
-    R = w["geometry"]["R"]
-    nu = (w["tau"] - 0.5) / 3.0
-    w0 = math.sqrt(8.0 * w["sigma"] / R ** 3)  # l (l - 1) (l + 2) = 8 for l = 2, rho = 1
-    gam = 5.0 * nu / R ** 2                      # (l - 1)(2 l + 1) nu / R^2
-    per = {"zero_crossings": [float(v) for v in zc], "samples_every": every, "steps": total,
-           "period_rayleigh": 2.0 * math.pi / w0,
-           "period_lamb_damped": 2.0 * math.pi / math.sqrt(max(w0 * w0 - gam * gam, 1e-30))}
-    if len(zc) >= 2:
-        per["period"] = 2.0 * float(np.mean(np.diff(zc)))
-        per["rel_err_lamb"] = abs(per["period"] - per["period_lamb_damped"]) / per["period_lamb_damped"]
-    out["oscillating256_period"] = per
+    # -- oscillation period, per storage form
+    per_all = {}
+    for storage in ("f32", "f16", "bf16"):
+        w = S.workload("oscillating256")
+        P, sim, phi0, obs = make_sim(F, w, "lsqr", storage, stream)
+        zz, yy, xx = torch.meshgrid(*[torch.arange(n, device="cuda", dtype=torch.float32) for n in w["shape"]],
+                                    indexing="ij")
+        every, total = 200, 36000
+        a = []
+        m0, l0 = sim.mass_total()
+        for k in range(total // every + 1):
+            if k:
+                sim.step(every)
+            wgt = _fill_weight(F, sim)
+            m = wgt.sum()
+            cx, cy, cz = (wgt * xx).sum() / m, (wgt * yy).sum() / m, (wgt * zz).sum() / m
+            izz = (wgt * (zz - cz) ** 2).sum() / m
+            ixy = 0.5 * ((wgt * (xx - cx) ** 2).sum() + (wgt * (yy - cy) ** 2).sum()) / m
+            a.append(float(izz - ixy))
+        m1, l1 = sim.mass_total()
+        sim.close()
+        del xx, yy, zz
+        zc = zero_crossings(a, every)
+        R = w["geometry"]["R"]
+        nu = (w["tau"] - 0.5) / 3.0
+        w0 = math.sqrt(8.0 * w["sigma"] / R ** 3)  # l (l - 1) (l + 2) = 8 for l = 2, rho = 1
+        gam = 5.0 * nu / R ** 2                      # (l - 1)(2 l + 1) nu / R^2
+        per = {"zero_crossings": [float(v) for v in zc], "samples_every": every, "steps": total,
+               "period_rayleigh": 2.0 * math.pi / w0,
+               "period_lamb_damped": 2.0 * math.pi / math.sqrt(max(w0 * w0 - gam * gam, 1e-30)),
+               "mass_drift_rel": ((m1 + l1) - (m0 + l0)) / (m0 + l0), "amplitude_first": a[0], "amplitude_last": a[-1]}
+        if len(zc) >= 2:
+            per["period"] = 2.0 * float(np.mean(np.diff(zc)))
+            per["rel_err_lamb"] = abs(per["period"] - per["period_lamb_damped"]) / per["period_lamb_damped"]
+        per_all[storage] = per
+        torch.cuda.empty_cache()
+    out["oscillating256_period"] = per_all
+    # -- Tab. advection (prescribed flow)
+    out["advection_table"] = advection_report(F, stream)
+    # -- Renardy bubble with the bubble model: static (short run) and moving frame
+    out["renardy_static_dx48"] = {m: renardy_bubble(F, stream, 48, m, 20000) for m in ("fd", "lsqr", "tr")}
+    out["renardy_moving_dx96"] = {m: renardy_bubble(F, stream, 96, m, 40000, moving=True, sample_every=4000)
+                                  for m in ("fd", "lsqr", "tr")}
     # -- all-liquid box: the liquid stream-collide alone
     shape = (256, 256, 256)
     P = F.make_params(shape, collision=F.BGK, tau=0.6)
@@ -844,6 +1018,19 @@ def run_fsl(args):
         curv_fd = {"ms": fd_ms, "evals_per_s": n_if_now / (fd_ms * 1e-3), "includes": "normals + smoothing + FD"}
     except Exception as e:  # a side figure: the headline line is printed regardless
         curv_fd = {"error": str(e)[:200]}
+    # ---- curvature alone (TR: triangle fan of PLIC points, Sec. II.B) on the same state
+    try:
+        sim.curvature(F.CURV_TR, kap)
+        for a, b in cev:
+            flush.fill_(1.0)
+            a.record(stream)
+            sim.curvature(F.CURV_TR, kap)
+            b.record(stream)
+        torch.cuda.synchronize()
+        tr_ms = sum(a.elapsed_time(b) for a, b in cev) / len(cev)
+        curv_tr = {"ms": tr_ms, "evals_per_s": n_if_now / (tr_ms * 1e-3), "includes": "normals + PLIC + fan"}
+    except Exception as e:
+        curv_tr = {"error": str(e)[:200]}
 
     # ---- mass reduction (FP64 partials) alone
     m0 = time.perf_counter()
@@ -881,7 +1068,7 @@ def run_fsl(args):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "fluid_cells": n_fluid, "interface_cells": n_if, "mlups_domain": N * args.steps / (ms * 1e-3) / 1e6,
             "curvature_evals_per_s": n_if_now / (curv_ms * 1e-3), "curvature_ms": curv_ms,
-            "curvature_fd": curv_fd,
+            "curvature_fd": curv_fd, "curvature_tr": curv_tr,
             "lsqr_fp64_cells": n_fp64,
             "phases_ms": dict(zip(PHASES, [round(float(v), 5) for v in ph])),
             "mass_reduce_ms": mass_ms, "mass_drift_rel": drift, "roofline": roof, "e2e": e2e,
@@ -904,8 +1091,14 @@ def run_fsl(args):
         lc = learned_curvature(F, S, stream, flush, peaks, S.SEED + rank, args.mlp_train, args.mlp_epochs,
                                min(args.steps, 100))
         held = lc.pop("heldout")
+        net = lc.pop("net")
         line["learned_curvature"] = lc
         line["adjoint"] = adjoint_window(F, S, stream, S.SEED + rank)
+        if not args.no_physics:
+            t_ph = time.perf_counter()
+            line["physics"] = physics_reports(F, S, stream, net)
+            line["physics"]["seconds"] = time.perf_counter() - t_ph
+        del net
     if gs is not None:
         line["cpu_baseline"] = oracle_sample(w, args.cpu_seconds, gpu_state=gs)
         line["cpu_all_cores"] = oracle_all_cores(w, min(args.cpu_seconds, 10.0))
@@ -935,6 +1128,7 @@ def main():
         lc = learned_curvature(F, S, torch.cuda.current_stream(), None, {}, S.SEED, args.mlp_train, args.mlp_epochs, 0,
                                inference=False)
         lc.pop("heldout")
+        lc.pop("net")
         print(json.dumps({"learned_curvature": lc}))
         return
     if args.physics:

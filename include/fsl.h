@@ -72,7 +72,7 @@ extern "C" {
 typedef struct fsl_ctx fsl_ctx; /* opaque */
 
 enum fsl_collision { FSL_BGK = 0, FSL_TRT = 1 };
-enum fsl_curv_model { FSL_CURV_LSQR = 0, FSL_CURV_FD = 1, FSL_CURV_NONE = 2, FSL_CURV_MLP = 3 };
+enum fsl_curv_model { FSL_CURV_LSQR = 0, FSL_CURV_FD = 1, FSL_CURV_NONE = 2, FSL_CURV_MLP = 3, FSL_CURV_TR = 4 };
 enum fsl_storage { FSL_F32 = 0, FSL_F16_OFS = 1, FSL_BF16_OFS = 2 };
 enum fsl_where { FSL_NONE = 0, FSL_HOST = 1, FSL_DEVICE = 2 };
 
@@ -93,6 +93,14 @@ typedef struct fsl_params {
     double lsqr_fp64_cond;  /* condition estimate of the LSQR normal equations A^T A,
                                (max R_jj / min R_jj)^2 of its FP32 factor, above which
                                the cell is re-solved in FP64 (e.g. 1e6) */
+    int32_t excess_rule;    /* excess mass of converted cells (the conversion rules the
+                               paper cites from Koerner et al.): 0 equal shares among the
+                               interface neighbours after conversion; 1 shares weighted
+                               by the cell's interface normal n (into the liquid): a
+                               filled cell gives max(0, -n.c_q), an emptied one
+                               max(0, n.c_q) to the receiver at x + c_q, equal shares
+                               if every weight is 0 */
+    int32_t pad_;
 } fsl_params;
 
 /* Caller-owned device buffers (all 256-byte aligned). */
@@ -152,7 +160,7 @@ int fsl_refresh(struct fsl_ctx *ctx);
 
 /* Checkpoint and resume (a service of this library; the paper has no
  * counterpart).  fsl_save writes the state of the context after all work
- * queued on its stream: a header (magic "FSLCKPT1", format version 1, nx, ny,
+ * queued on its stream: a header (magic "FSLCKPT1", format version 2, nx, ny,
  * nz, storage, storage_shift, the lost-mass counter, the context's
  * fsl_params), then the current PDF buffer f[parity] (19 N values in the
  * storage type, f[q N + i]), the cell types (N bytes, type bits only), mass
@@ -182,9 +190,13 @@ int fsl_step(struct fsl_ctx *ctx, int nsteps);
 
 /* Curvature of the current state by `model` (Sec. II.A FD with K8 smoothing
  * and wetting normals, Eq. contactNormal; Sec. II.C LSQR paraboloid fit to
- * PLIC points with contact-point rows/constraints, Eq. contactConstraint),
- * written to kappa_out (N floats, device; interface cells only; may be
- * fields->kappa).  Asynchronous. */
+ * PLIC points with contact-point rows/constraints, Eq. contactConstraint;
+ * Sec. II.B TR: a triangle fan of the PLIC points of the 3x3x3 block around
+ * the centre point, ordered by angle in its tangent plane, and the mean of
+ * the directional curvatures 2h/|p|^2 weighted by the areas of the fan
+ * triangles at each edge, without a wetting treatment), written to kappa_out
+ * (N floats, device; interface cells only; may be fields->kappa).
+ * Asynchronous. */
 int fsl_curvature(struct fsl_ctx *ctx, int model, float *kappa_out);
 
 /* Total mass sum_interface m + sum_liquid rho, and the mass lost by
@@ -198,6 +210,44 @@ int fsl_mass(struct fsl_ctx *ctx, double *total_mass, double *lost_mass);
  * cells the learned curvature evaluated and cells where its value was kept
  * (last FSL_CURV_MLP pass).  Synchronising. */
 int fsl_stats(struct fsl_ctx *ctx, int64_t counts_out[10]);
+
+/* Bubble model (Sec. III.A: the gas is not simulated; its pressure follows
+ * the gas volume).  With p0 > 0 the gas pressure of every step is
+ * p_g = p0 V0 / V (isothermal ideal gas), V the gas volume of the state the
+ * step starts from: non-obstacle cells minus liquid cells minus the sum of
+ * the interface fill levels (gas cells count 1, interface cells 1 - phi).
+ * V0 > 0 sets the reference volume, V0 <= 0 takes the current one.  The
+ * volume is counted from the state here and by fsl_refresh / fsl_load, and
+ * tracked by the step's own kernels in between (integer fixed-point sums, so
+ * it does not depend on the order of additions).  It is one total: several
+ * separate bubbles share one pressure.  p0 = 0 switches the model off
+ * (params.p_gas applies again).  Adjoint windows are unsupported while it is
+ * on.  Synchronising; FSL_EINVAL for p0 < 0 or a state without gas. */
+int fsl_set_bubble(struct fsl_ctx *ctx, double p0, double V0);
+
+/* Gas volume of the current state and the gas pressure the next step uses
+ * (bubble model on; FSL_EINVAL otherwise).  Synchronising. */
+int fsl_bubble(struct fsl_ctx *ctx, double *volume, double *p_gas);
+
+/* Prescribed flow for the advection test of Sec. III.A (Tab. advection):
+ * sets the current post-collision PDFs of every liquid and interface cell to
+ * the equilibrium feq(rho, u) (standard second-order D3Q19 form), so that the
+ * next fsl_step moves the fill level through the mass exchange of Eqs.
+ * (advection1/2) and the conversions in a constant flow; calling it before
+ * every step keeps the lattice Boltzmann data constant.  rho > 0.
+ * Asynchronous. */
+int fsl_prescribe_flow(struct fsl_ctx *ctx, double rho, double ux, double uy, double uz);
+
+/* Conversions of the last fsl_step (Sec. II; the rules the paper cites from
+ * Koerner et al., see fsl_step): counts_out[0..3] = cells that filled
+ * (interface -> liquid), emptied (interface -> gas; a candidate kept at the
+ * interface by a filling neighbour is not counted), became interface from
+ * gas, and became interface from liquid.  If cells_out is not NULL the cell
+ * indices of the four sets follow one another there, each set in ascending
+ * order (host memory, capacity entries; FSL_ECAPACITY if they do not fit).
+ * Valid until the next fsl_step or fsl_curvature; zero after fsl_init,
+ * fsl_refresh and fsl_load.  Synchronising. */
+int fsl_conversions(struct fsl_ctx *ctx, int64_t counts_out[4], int32_t *cells_out, int64_t capacity);
 
 /* One time step like fsl_step(ctx, 1), launched kernel by kernel (no graph,
  * phases in sequence) with CUDA events on the context's stream between its

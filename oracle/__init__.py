@@ -38,6 +38,10 @@ Parity status of the oracle functions
                               for a bubble compressed by a liquid at higher
                               pressure (the bubble shrinks until p_g matches it)
   conversion readings         pinned on flat-interface scenarios whose outcome
+                              (equal shares, and the normal-weighted shares of
+                              reading K1: 1/5 to the new cells on the gas side
+                              of a filled cell, 1/5 to the cells from liquid on
+                              the liquid side of an emptied one)
                               follows from the readings by counting (thresholds,
                               filling beats emptying, new cells from gas and
                               from liquid, 13 equal excess shares, new cells at
@@ -82,7 +86,7 @@ class Params(ctypes.Structure):
                 ("collision", ctypes.c_int), ("curv_model", ctypes.c_int), ("literal_phi", ctypes.c_int),
                 ("tau", ctypes.c_double), ("magic", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("p_gas", ctypes.c_double), ("theta", ctypes.c_double), ("eps", ctypes.c_double),
-                ("frozen", ctypes.c_int)]
+                ("frozen", ctypes.c_int), ("excess_rule", ctypes.c_int)]
 
 
 class Geom(ctypes.Structure):
@@ -156,11 +160,13 @@ def lattice():
 
 
 def params(shape, collision=0, curv_model=0, tau=1.0, magic=3.0 / 16.0, sigma=0.0, p_gas=1.0 / 3.0,
-           theta=np.pi / 2, eps=1e-3, literal_phi=0, frozen=0) -> Params:
+           theta=np.pi / 2, eps=1e-3, literal_phi=0, frozen=0, excess_rule=0) -> Params:
     """shape = (nz, ny, nx) of the numpy arrays (x fastest).  frozen = 1: cell
-    types frozen (no conversion test), as in the adjoint windows."""
+    types frozen (no conversion test), as in the adjoint windows.
+    excess_rule = 1: excess mass shared by normal-weighted shares (reading K1)."""
     nz, ny, nx = shape
-    return Params(nx, ny, nz, collision, curv_model, literal_phi, tau, magic, sigma, p_gas, theta, eps, frozen)
+    return Params(nx, ny, nz, collision, curv_model, literal_phi, tau, magic, sigma, p_gas, theta, eps, frozen,
+                  excess_rule)
 
 
 def feq(q, rho, u):

@@ -52,6 +52,7 @@ typedef struct {
     double theta;    /* equilibrium contact angle theta_eq in radians */
     double eps;      /* conversion threshold */
     int frozen;      /* 1 = cell types frozen: no conversion test, no excess mass */
+    int excess_rule; /* 0 = equal shares (reading O7), 1 = normal-weighted shares (reading K1) */
 } orc_params;
 
 typedef struct {
@@ -1019,7 +1020,12 @@ void orc_step(const orc_params *P, const double *fin, double *fout, uint8_t *fla
             mnew[y] = rho[y];
         }
     }
-    /* excess mass, shared equally by the interface cells after conversion */
+    /* excess mass, shared by the interface cells after conversion: equally
+     * (reading O7), or weighted by the interface normal (reading K1, after
+     * Koerner et al.: a filled cell gives to the gas side, weight
+     * max(0, -n.c_q), an emptied one to the liquid side, max(0, n.c_q), n the
+     * PLIC normal of the cell at t (pointing into the liquid), c_q the
+     * lattice vector to the receiver; equal shares if every weight is 0) */
     for (long x = 0; x < N; ++x) {
         if (!conv[x]) continue;
         double mex;
@@ -1031,9 +1037,18 @@ void orc_step(const orc_params *P, const double *fin, double *fout, uint8_t *fla
             mnew[x] = 0;
         }
         int n = 0;
+        double W = 0, wq[NQ];
+        const double *nx4 = normal4 + 4 * x;
+        const double sgn = conv[x] == 1 ? -1.0 : 1.0;
         for (int q = 1; q < NQ; ++q) {
             long y = nbr(P, x, CXQ[q], CYQ[q], CZQ[q]);
-            if (((ft[y] & FL_IF) && !conv[y]) || newif[y]) ++n;
+            wq[q] = 0;
+            if (((ft[y] & FL_IF) && !conv[y]) || newif[y]) {
+                ++n;
+                double nc = nx4[0] * CXQ[q] + nx4[1] * CYQ[q] + nx4[2] * CZQ[q];
+                wq[q] = fmax(0.0, sgn * nc);
+                W += wq[q];
+            }
         }
         if (n == 0) {
             *lost += mex;
@@ -1041,7 +1056,9 @@ void orc_step(const orc_params *P, const double *fin, double *fout, uint8_t *fla
         }
         for (int q = 1; q < NQ; ++q) {
             long y = nbr(P, x, CXQ[q], CYQ[q], CZQ[q]);
-            if (((ft[y] & FL_IF) && !conv[y]) || newif[y]) mnew[y] += mex / n;
+            if (!(((ft[y] & FL_IF) && !conv[y]) || newif[y])) continue;
+            if (P->excess_rule == 1 && W > 0) mnew[y] += mex * (wq[q] / W);
+            else mnew[y] += mex / n;
         }
     }
     for (long x = 0; x < N; ++x) {

@@ -5,6 +5,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include <new>
 
 #include "adjoint.cuh"
@@ -26,6 +29,7 @@ struct fsl_ctx {
     double *host_mass;       // pinned, 4 doubles (mass, lost; dL/dsigma, dL/dtheta)
     long long *host_stats;   // pinned
     int *host_count;         // pinned, 1 int
+    int bubble;              // bubble model on (fsl_set_bubble)
     // the last adjoint window (fsl_window_forward)
     void *adj_ws;
     int adj_window, adj_ckpt, adj_cap, adj_valid;
@@ -37,11 +41,14 @@ constexpr size_t ALIGN = 256;
 size_t up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t normal, rho, excess, rmark, iflist0, iflist1, fill, empty, newgas, liq2if, slow, seg_active, seg_list, counts,
-        lost, status, partial, stats, mass_out, total;
+    size_t normal, rho, excess, exw, rmark, iflist0, iflist1, fill, empty, newgas, liq2if, slow, seg_active, seg_list, counts,
+        lost, status, partial, stats, mass_out, bubble, brick0, brick1, brick_tag, total;
 };
 
 size_t nseg_of(const fsl_params &p) { return (size_t)((p.nx + SEG - 1) / SEG) * p.ny * p.nz; }
+size_t nbrick_of(const fsl_params &p) {
+    return (size_t)((p.nx + BRK - 1) / BRK) * ((p.ny + BRK - 1) / BRK) * ((p.nz + BRK - 1) / BRK);
+}
 
 Layout layout(const fsl_params &p) {
     const size_t N = (size_t)p.nx * p.ny * p.nz;
@@ -50,6 +57,7 @@ Layout layout(const fsl_params &p) {
     L.normal = o; o += up(N * sizeof(float4));
     L.rho = o; o += up(N * sizeof(float));
     L.excess = o; o += up(N * sizeof(float));
+    L.exw = o; o += up(N * sizeof(float));
     L.rmark = o; o += up(N);
     L.iflist0 = o; o += up(N * sizeof(int));
     L.iflist1 = o; o += up(N * sizeof(int));
@@ -66,6 +74,10 @@ Layout layout(const fsl_params &p) {
     L.partial = o; o += up((size_t)max_partials() * sizeof(double));
     L.stats = o; o += up(16 * sizeof(long long));
     L.mass_out = o; o += up(2 * sizeof(double));
+    L.bubble = o; o += up(8 * sizeof(long long) + 2 * sizeof(double) + sizeof(float));
+    L.brick0 = o; o += up(nbrick_of(p) * sizeof(int));
+    L.brick1 = o; o += up(nbrick_of(p) * sizeof(int));
+    L.brick_tag = o; o += up(nbrick_of(p) * sizeof(int));
     L.total = o;
     return L;
 }
@@ -77,7 +89,7 @@ bool valid_params(const fsl_params *p) {
     if (N >= 2147483647.0) return false;  // cell indices are int32 in the lists
     if (p->nx > 65535 * 256 || p->ny > 65535 || p->nz > 65535) return false;
     if (p->collision != FSL_BGK && p->collision != FSL_TRT) return false;
-    if (p->curv_model < FSL_CURV_LSQR || p->curv_model > FSL_CURV_MLP) return false;
+    if (p->curv_model < FSL_CURV_LSQR || p->curv_model > FSL_CURV_TR) return false;
     if (p->storage < FSL_F32 || p->storage > FSL_BF16_OFS) return false;
     if (p->storage != FSL_F32 && (p->storage_shift < 0 || p->storage_shift > 24)) return false;
     if (!(p->tau > 0.5) || !isfinite(p->tau)) return false;
@@ -85,6 +97,7 @@ bool valid_params(const fsl_params *p) {
     if (p->plic_iters < 1 || p->plic_iters > 64) return false;
     if (!isfinite(p->sigma) || !isfinite(p->p_gas) || !isfinite(p->theta) || !(p->eps_convert >= 0.0)) return false;
     if (!(p->lsqr_fp64_cond > 1.0)) return false;
+    if (p->excess_rule != 0 && p->excess_rule != 1) return false;
     return true;
 }
 
@@ -105,6 +118,8 @@ Dev make_dev(const fsl_params &p, const fsl_fields &f) {
     d.normal = reinterpret_cast<float4 *>(ws + L.normal);
     d.rho = reinterpret_cast<float *>(ws + L.rho);
     d.excess = reinterpret_cast<float *>(ws + L.excess);
+    d.exw = reinterpret_cast<float *>(ws + L.exw);
+    d.excess_rule = p.excess_rule;
     d.rmark = reinterpret_cast<uint8_t *>(ws + L.rmark);
     d.iflist = reinterpret_cast<int *>(ws + L.iflist0);
     d.iflist_next = reinterpret_cast<int *>(ws + L.iflist1);
@@ -112,6 +127,17 @@ Dev make_dev(const fsl_params &p, const fsl_fields &f) {
     d.seg_list = reinterpret_cast<int *>(ws + L.seg_list);
     d.nsegx = (p.nx + SEG - 1) / SEG;
     d.nseg = (int)nseg_of(p);
+    d.nbx = (p.nx + BRK - 1) / BRK;
+    d.nby = (p.ny + BRK - 1) / BRK;
+    d.nbz = (p.nz + BRK - 1) / BRK;
+    d.brick_tag = reinterpret_cast<int *>(ws + L.brick_tag);
+    // counter slots of list parity 0 (dev_for and the window view set their own)
+    d.cif = C_IF0;
+    d.cif_next = C_IF1;
+    d.cdirty = C_SEGD0;
+    d.cdirty_next = C_SEGD1;
+    d.cbrk = C_BRK0;
+    d.cbrk_next = C_BRK1;
     d.fill = reinterpret_cast<int *>(ws + L.fill);
     d.empty = reinterpret_cast<int *>(ws + L.empty);
     d.newgas = reinterpret_cast<int *>(ws + L.newgas);
@@ -158,6 +184,11 @@ Dev dev_for(const fsl_ctx *c, int parity) {
     d.cif_next = C_IF0 + (parity ^ 1);
     d.cdirty = C_SEGD0 + parity;
     d.cdirty_next = C_SEGD0 + (parity ^ 1);
+    int *bricks[2] = {reinterpret_cast<int *>(ws + L.brick0), reinterpret_cast<int *>(ws + L.brick1)};
+    d.brick_list = bricks[parity];
+    d.brick_list_next = bricks[parity ^ 1];
+    d.cbrk = C_BRK0 + parity;
+    d.cbrk_next = C_BRK0 + (parity ^ 1);
     return d;
 }
 
@@ -171,6 +202,7 @@ void enqueue_curvature(const Dev &d, int model, float *kappa_out, cudaStream_t s
     launch_normals(d, s);
     if (model == FSL_CURV_LSQR || model == FSL_CURV_MLP) launch_lsqr(d, kappa_out, s);
     else if (model == FSL_CURV_FD) launch_fd(d, kappa_out, s);
+    else if (model == FSL_CURV_TR) launch_tr(d, kappa_out, s);
     else launch_zero_kappa(d, kappa_out, s);
     if (model == FSL_CURV_MLP) launch_mlp_curv(d, kappa_out, s);
 }
@@ -187,8 +219,8 @@ int enqueue_step_graph(const fsl_ctx *c, int parity) {
     launch_sc_bulk(d, side);
     CK(cudaEventRecord(c->join, side));
     if (c->p.curv_model == FSL_CURV_LSQR) {
-        launch_normals(d, s);
-        launch_curv_iface(d, s);
+        launch_step_begin(d, s);
+        launch_curv_iface(d, s);  // normals, fit and interface stream-collide per brick
     } else {
         enqueue_curvature(d, c->p.curv_model, d.kappa, s);
         launch_sc_iface(d, s);
@@ -283,6 +315,10 @@ Dev window_dev(const fsl_ctx *c, char *ws, const AdjLayout &A) {
     d.cif_next = C_IF1;
     d.cdirty = C_SEGD0;
     d.cdirty_next = C_SEGD1;
+    d.cbrk = C_BRK0;  // no brick list in a window: the frozen step runs the list kernels
+    d.cbrk_next = C_BRK1;
+    d.brick_list = nullptr;
+    d.brick_list_next = nullptr;
     d.seg_list = reinterpret_cast<int *>(ws + A.wseg);
     d.frozen = 1;
     return d;
@@ -412,6 +448,8 @@ int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *ph
         d0.fdst = fields->f[0];
         launch_init_state(d0, fields->flags[1], s);
         launch_seg_compact(d0, s);
+        if (cudaMemsetAsync(c->base.brick_tag, 0xff, nbrick_of(c->p) * sizeof(int), s) != cudaSuccess) break;
+        launch_brick_build(d0, s);
         // the second buffer starts as a copy, so every cell of both buffers
         // holds a defined value (w_q away from the fluid) from here on
         const size_t fbytes = (size_t)Q * N * pdf_elem_bytes(c->p.storage);
@@ -437,6 +475,12 @@ int fsl_refresh(fsl_ctx *c) {
     CK(cudaMemsetAsync(d.rmark, 0, d.N, c->stream));
     launch_refresh(d, c->stream);
     launch_seg_compact(d, c->stream);
+    CK(cudaMemsetAsync(d.brick_tag, 0xff, nbrick_of(c->p) * sizeof(int), c->stream));
+    launch_brick_build(d, c->stream);
+    if (c->bubble) {  // the caller may have changed the liquid volume: recount it
+        CK(cudaMemsetAsync(c->base.bub_i, 0, 5 * sizeof(long long), c->stream));
+        launch_bubble_count(d, c->stream);
+    }
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
 }
 
@@ -466,12 +510,14 @@ int fsl_step_profile(fsl_ctx *c, float ms_out[6]) {
     int rc = FSL_ECUDA;
     do {
         if (cudaEventRecord(ev[0], s) != cudaSuccess) break;
-        launch_normals(d, s);
-        if (cudaEventRecord(ev[1], s) != cudaSuccess) break;
         const bool fused = c->p.curv_model == FSL_CURV_LSQR;
+        if (fused) launch_step_begin(d, s);  // the normals are part of the brick pass
+        else launch_normals(d, s);
+        if (cudaEventRecord(ev[1], s) != cudaSuccess) break;
         if (fused) launch_curv_iface(d, s);  // curvature + interface stream-collide
         else if (c->p.curv_model == FSL_CURV_MLP) launch_lsqr(d, d.kappa, s);
         else if (c->p.curv_model == FSL_CURV_FD) launch_fd(d, d.kappa, s);
+        else if (c->p.curv_model == FSL_CURV_TR) launch_tr(d, d.kappa, s);
         else launch_zero_kappa(d, d.kappa, s);
         if (c->p.curv_model == FSL_CURV_MLP) launch_mlp_curv(d, d.kappa, s);
         if (cudaEventRecord(ev[2], s) != cudaSuccess) break;
@@ -493,7 +539,7 @@ int fsl_step_profile(fsl_ctx *c, float ms_out[6]) {
 }
 
 int fsl_curvature(fsl_ctx *c, int model, float *kappa_out) {
-    if (!c || !kappa_out || model < FSL_CURV_LSQR || model > FSL_CURV_MLP) return FSL_EINVAL;
+    if (!c || !kappa_out || model < FSL_CURV_LSQR || model > FSL_CURV_TR) return FSL_EINVAL;
     if (model == FSL_CURV_MLP && !c->base.mlp_params) return FSL_EINVAL;
     const Dev d = dev_for(c, c->parity);
     enqueue_curvature(d, model, kappa_out, c->stream);
@@ -541,6 +587,110 @@ int fsl_stats(fsl_ctx *c, int64_t counts_out[10]) {
     return FSL_OK;
 }
 
+// gas volume of the current state from the bubble counters (synchronising)
+static int bubble_volume(fsl_ctx *c, double *V) {
+    long long b[5];
+    CK(cudaMemcpyAsync(b, c->base.bub_i, sizeof b, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int par = c->parity;
+    *V = (double)(b[4] - b[par]) - (double)b[2 + par] / BUB_FIX;
+    return FSL_OK;
+}
+
+int fsl_set_bubble(fsl_ctx *c, double p0, double V0) {
+    if (!c || !isfinite(p0) || !isfinite(V0) || p0 < 0.0) return FSL_EINVAL;
+    for (int k = 0; k < 2; ++k)  // recorded graphs hold the old kernel arguments
+        if (c->graph[k]) {
+            cudaGraphExecDestroy(c->graph[k]);
+            c->graph[k] = nullptr;
+        }
+    c->adj_valid = 0;
+    if (p0 == 0.0) {
+        c->bubble = 0;
+        c->base.bub_i = nullptr;
+        c->base.bub_d = nullptr;
+        c->base.bub_rho = nullptr;
+        return FSL_OK;
+    }
+    const Layout L = layout(c->p);
+    char *bw = static_cast<char *>(c->fields.workspace) + L.bubble;
+    c->base.bub_i = reinterpret_cast<long long *>(bw);
+    c->base.bub_d = reinterpret_cast<double *>(bw + 8 * sizeof(long long));
+    c->base.bub_rho = reinterpret_cast<float *>(bw + 8 * sizeof(long long) + 2 * sizeof(double));
+    c->bubble = 1;
+    const Dev d = dev_for(c, c->parity);
+    CK(cudaMemsetAsync(c->base.bub_i, 0, 8 * sizeof(long long), c->stream));
+    launch_bubble_count(d, c->stream);
+    double V = 0.0;
+    const int rc = bubble_volume(c, &V);
+    if (rc != FSL_OK) return rc;
+    const double pd[2] = {p0, V0 > 0.0 ? V0 : V};
+    if (!(pd[1] > 0.0)) return FSL_EINVAL;  // no gas in the state
+    const float r0 = (float)(3.0 * p0 * pd[1] / V);
+    CK(cudaMemcpyAsync(c->base.bub_d, pd, sizeof pd, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->base.bub_rho, &r0, sizeof r0, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FSL_OK;
+}
+
+int fsl_bubble(fsl_ctx *c, double *volume, double *p_gas) {
+    if (!c || !c->bubble) return FSL_EINVAL;
+    double V = 0.0;
+    const int rc = bubble_volume(c, &V);
+    if (rc != FSL_OK) return rc;
+    double pd[2];
+    CK(cudaMemcpy(pd, c->base.bub_d, sizeof pd, cudaMemcpyDeviceToHost));
+    if (volume) *volume = V;
+    if (p_gas) *p_gas = V > 0.0 ? pd[0] * pd[1] / V : c->p.p_gas;
+    return FSL_OK;
+}
+
+int fsl_prescribe_flow(fsl_ctx *c, double rho, double ux, double uy, double uz) {
+    if (!c || !(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz)) return FSL_EINVAL;
+    Dev d = dev_for(c, c->parity);
+    d.fdst = c->fields.f[c->parity];  // the current buffer: what the next step streams from
+    launch_prescribe(d, (float)rho, (float)ux, (float)uy, (float)uz, c->stream);
+    return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
+}
+
+int fsl_conversions(fsl_ctx *c, int64_t counts_out[4], int32_t *cells_out, int64_t capacity) {
+    if (!c || !counts_out || (cells_out && capacity < 0)) return FSL_EINVAL;
+    const Dev d = dev_for(c, c->parity);
+    int cnt[C_NCOUNT];
+    CK(cudaMemcpyAsync(cnt, d.counts, sizeof cnt, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int *lists[4] = {d.fill, d.empty, d.newgas, d.liq2if};
+    const int n[4] = {cnt[C_FILL], cnt[C_EMPTY], cnt[C_NEWGAS], cnt[C_LIQ2IF]};
+    std::vector<int32_t> v[4];
+    for (int k = 0; k < 4; ++k) {
+        if (n[k] < 0 || n[k] > c->base.N) return FSL_ECUDA;
+        v[k].resize((size_t)n[k]);
+        if (n[k]) CK(cudaMemcpy(v[k].data(), lists[k], (size_t)n[k] * sizeof(int), cudaMemcpyDeviceToHost));
+    }
+    // an emptying candidate that a filling neighbour kept at the interface is
+    // not emptied: keep the candidates whose type after the step is gas
+    std::vector<int32_t> emptied;
+    for (int32_t i : v[1]) {
+        uint8_t f = 0;
+        CK(cudaMemcpy(&f, c->fields.flags[0] + i, 1, cudaMemcpyDeviceToHost));
+        if ((f & T_MASK) == T_GAS) emptied.push_back(i);
+    }
+    v[1].swap(emptied);
+    int64_t total = 0;
+    for (int k = 0; k < 4; ++k) {
+        std::sort(v[k].begin(), v[k].end());
+        counts_out[k] = (int64_t)v[k].size();
+        total += counts_out[k];
+    }
+    if (!cells_out) return FSL_OK;
+    if (total > capacity) return FSL_ECAPACITY;
+    for (int k = 0; k < 4; ++k) {
+        memcpy(cells_out, v[k].data(), v[k].size() * sizeof(int32_t));
+        cells_out += v[k].size();
+    }
+    return FSL_OK;
+}
+
 size_t fsl_adjoint_workspace_size(const fsl_params *params, int window, int ckpt_every, int max_interface) {
     if (!valid_params(params) || window < 1 || ckpt_every < 1 || max_interface < 1) return 0;
     const int K = ckpt_every < window ? ckpt_every : window;
@@ -567,7 +717,7 @@ int fsl_set_surface(fsl_ctx *c, double sigma, double theta) {
 
 int fsl_window_forward(fsl_ctx *c, int window, int ckpt_every, int max_interface, void *adj_ws, size_t adj_bytes) {
     if (!c || window < 1 || ckpt_every < 1 || max_interface < 1 || !aligned(adj_ws)) return FSL_EINVAL;
-    if (!adjoint_supported(c->p)) return FSL_EUNSUPPORTED;
+    if (!adjoint_supported(c->p) || c->bubble) return FSL_EUNSUPPORTED;
     const int K = ckpt_every < window ? ckpt_every : window;
     const AdjLayout A = adj_layout(c->p, window, K, max_interface);
     if (adj_bytes < A.total) return FSL_EINVAL;
@@ -722,7 +872,7 @@ int fsl_save(fsl_ctx *c, const char *path) {
     CkptHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, "FSLCKPT1", 8);
-    h.version = 1;
+    h.version = 2;  // 2: fsl_params with excess_rule
     h.nx = c->p.nx;
     h.ny = c->p.ny;
     h.nz = c->p.nz;
@@ -764,7 +914,7 @@ int fsl_load(fsl_ctx *c, const char *path) {
     FILE *fp = fopen(path, "rb");
     if (!fp) return FSL_EIO;
     CkptHeader h;
-    bool ok = fread(&h, sizeof h, 1, fp) == 1 && memcmp(h.magic, "FSLCKPT1", 8) == 0 && h.version == 1 &&
+    bool ok = fread(&h, sizeof h, 1, fp) == 1 && memcmp(h.magic, "FSLCKPT1", 8) == 0 && h.version == 2 &&
               h.nx == c->p.nx && h.ny == c->p.ny && h.nz == c->p.nz && h.storage == c->p.storage &&
               h.storage_shift == c->p.storage_shift;
     char *buf = ok ? static_cast<char *>(malloc(body ? body : 1)) : nullptr;

@@ -488,6 +488,23 @@ struct GridAcc {
 // path) when a contact-line cell is present, when there are fewer than five
 // rows, or when the Cholesky pivots estimate cond(A^T A) above fp64_cond.
 // In three parts so that the rows can be split over several lanes:
+// fill level at any cell (periodic wrap); an obstacle cell takes the
+// reflected fill level of Sec. II.A (kept out of line: callers unroll over
+// their stencils and obstacle cells are rare)
+static __device__ __noinline__ float phi_reflected(const Dev &d, int x, int y, int z) {
+    return reflect_value<float>([&](int a, int b, int c) { return d.flags[nbr_index(d, x, y, z, a, b, c)]; },
+                                [&](int a, int b, int c) { return d.phi[nbr_index(d, x, y, z, a, b, c)]; });
+}
+
+static __device__ __forceinline__ float phi_ext(const Dev &d, int x, int y, int z) {
+    x = wrap(x, d.nx);
+    y = wrap(y, d.ny);
+    z = wrap(z, d.nz);
+    const int i = cell_index(d, x, y, z);
+    if (!(d.flags[i] & T_OBS)) return d.phi[i];
+    return phi_reflected(d, x, y, z);
+}
+
 // lsqr_fast_frame, lsqr_fast_row (for each neighbour slot t of the 3x3x3
 // block, t = (dz+1)*9 + (dy+1)*3 + (dx+1), centre 13), lsqr_fast_solve.
 struct FastFrame {

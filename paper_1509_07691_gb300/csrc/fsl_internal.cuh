@@ -49,8 +49,14 @@ enum : uint8_t {
 // buffers, conversion lists, FP64 LSQR re-solves, active segments, and the
 // two "segment set changed" flags (one per step parity: a step sets its own,
 // clears the next step's, and rebuilds the segment list only if it is set)
+// (C_BRK0/1: lengths of the two brick lists; C_TAG: step tag of the brick marks)
 enum { C_IF0 = 0, C_IF1 = 1, C_FILL = 2, C_EMPTY = 3, C_NEWGAS = 4, C_LIQ2IF = 5, C_FP64 = 6, C_SEG = 7, C_SLOW = 8,
-       C_MLP = 9, C_MLPKEEP = 10, C_ADJ64 = 11, C_SEGD0 = 12, C_SEGD1 = 13, C_NCOUNT = 16 };
+       C_MLP = 9, C_MLPKEEP = 10, C_ADJ64 = 11, C_SEGD0 = 12, C_SEGD1 = 13, C_BRK0 = 14, C_BRK1 = 15, C_TAG = 16,
+       C_NCOUNT = 20 };
+
+// bricks of BRK^3 cells: the LSQR step's interface pass runs one block per
+// brick that holds interface cells
+constexpr int BRK = 8;
 
 // the grid is walked in x-row segments of SEG cells (one warp each); a
 // segment is active while it holds a liquid or interface cell
@@ -98,6 +104,7 @@ struct Dev {
     void *fdst;        // post-collision PDFs at t+1
     uint8_t *flags;    // cell types (+ transient bits during a step), updated in place
     float *mass, *phi, *kappa, *rho, *excess;
+    float *exw;        // 1: the converted cell's excess is shared by normal weights (else equally)
     float4 *normal;
     int *iflist;       // interface cells at t
     int *iflist_next;  // interface cells at t+1 (built by the step)
@@ -109,6 +116,12 @@ struct Dev {
     uint8_t *rmark;    // 1: the cell receives excess mass in this step's final update (0 between steps)
     int *seg_list;
     int nsegx, nseg;
+    // bricks holding interface cells at t and at t+1 (built by the final update),
+    // their counters, and the per-brick tag of the step that listed it last
+    int *brick_list, *brick_list_next;
+    int cbrk, cbrk_next;
+    int *brick_tag;
+    int nbx, nby, nbz;
     int *counts;
     double *lost;
     int *status;
@@ -117,6 +130,7 @@ struct Dev {
     // method parameters
     int collision, storage, plic_iters, curv_model;
     int frozen;              // 1: cell types frozen (no conversion test; adjoint windows)
+    int excess_rule;         // 0 equal excess shares, 1 normal-weighted shares
     float omega_e, omega_o;  // 1/tau_even, 1/tau_odd
     float rho_gas, six_sigma, eps;
     float cos_theta, sin_theta;
@@ -126,7 +140,58 @@ struct Dev {
     // learned curvature (FSL_CURV_MLP): packed parameters, judge tolerance
     const uint8_t *mlp_params;
     float mlp_rel;
+    // bubble model (gas pressure from the gas volume), off when bub_rho is null:
+    // bub_i[0..1] liquid cells of the state of each list parity, bub_i[2..3]
+    // sum of phi over its interface cells in fixed point (2^-32), bub_i[4]
+    // non-obstacle cells; bub_d[0..1] = p0, V0; *bub_rho = 3 p_g of the step
+    long long *bub_i;
+    double *bub_d;
+    float *bub_rho;
 };
+
+// fixed-point scale of the bubble model's fill-level sum (integer atomics keep
+// the sum independent of the order of the additions)
+constexpr double BUB_FIX = 4294967296.0;
+
+// 3 p_g of this step: the bubble model's value, else the constant parameter
+__device__ __forceinline__ float gas_density(const Dev &d) { return d.bub_rho ? __ldcg(d.bub_rho) : d.rho_gas; }
+
+// weight of the receiver at x + c of the excess mass of a converted cell with
+// interface normal n (into the liquid): a filled cell gives to the gas side,
+// an emptied one to the liquid side
+__device__ __forceinline__ float excess_weight(const float4 n, bool filled, int ccx, int ccy, int ccz) {
+    const float nc = n.x * ccx + n.y * ccy + n.z * ccz;
+    return fmaxf(0.f, filled ? -nc : nc);
+}
+
+// list parity of the step that d describes (0 or 1)
+__device__ __forceinline__ int list_parity(const Dev &d) { return d.cif - C_IF0; }
+
+__device__ __forceinline__ int brick_of(const Dev &d, int x, int y, int z) {
+    return x / BRK + d.nbx * (y / BRK + d.nby * (z / BRK));
+}
+
+// Work at the start of a step (or of a curvature pass), by one thread, before
+// any kernel of the step appends to a list: zero the step's counters and the
+// counters of the lists the final update builds, advance the brick tag, and
+// with the bubble model set this step's gas density 3 p_g = 3 p0 V0 / V from
+// the gas volume V = non-obstacle cells - liquid cells - interface fill levels
+// of the state the step starts from.
+__device__ __forceinline__ void step_prologue(const Dev &d) {
+    const int zero[8] = {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF, C_SLOW, C_FP64, C_MLP, C_MLPKEEP};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) d.counts[zero[k]] = 0;
+    d.counts[d.cif_next] = 0;
+    d.counts[d.cdirty_next] = 0;
+    d.counts[d.cbrk_next] = 0;
+    d.counts[C_TAG] += 1;
+    if (d.bub_i) {
+        const int par = list_parity(d);
+        const double V = (double)(d.bub_i[4] - d.bub_i[par]) - (double)d.bub_i[2 + par] / BUB_FIX;
+        *d.bub_rho = V > 0.0 ? (float)(3.0 * d.bub_d[0] * d.bub_d[1] / V) : d.rho_gas;
+        d.bub_i[2 + (par ^ 1)] = 0;  // the next state's sum, accumulated by the final update
+    }
+}
 
 // ---- PDF storage -----------------------------------------------------------
 template <int S>
@@ -258,6 +323,8 @@ void launch_fill_geometry(const fsl_params &p, const fsl_geometry &g, float *phi
 void launch_init_types(const Dev &d, const uint8_t *obstacle, uint8_t *tmp, cudaStream_t s);
 void launch_init_state(const Dev &d, const uint8_t *tmp, cudaStream_t s);
 void launch_refresh(const Dev &d, cudaStream_t s);
+// f' = feq(rho, u) at the liquid and interface cells of the buffer d.fdst
+void launch_prescribe(const Dev &d, float rho, float ux, float uy, float uz, cudaStream_t s);
 void launch_seg_compact(const Dev &d, cudaStream_t s);
 void launch_stats(const Dev &d, cudaStream_t s);
 void launch_mass(const Dev &d, double *out, cudaStream_t s);
@@ -271,6 +338,7 @@ void launch_finalize(const Dev &d, cudaStream_t s);
 void launch_normals(const Dev &d, cudaStream_t s);
 void launch_lsqr(const Dev &d, float *kappa_out, cudaStream_t s);
 void launch_fd(const Dev &d, float *kappa_out, cudaStream_t s);
+void launch_tr(const Dev &d, float *kappa_out, cudaStream_t s);
 void launch_zero_kappa(const Dev &d, float *kappa_out, cudaStream_t s);
 void launch_mlp_curv(const Dev &d, float *kappa_out, cudaStream_t s);
 // batch forward of the MLP on the tcgen05 tensor cores (k_mlp_tc.cu)
@@ -285,6 +353,13 @@ int launch_mlp_delta_tc(const uint8_t *params, const float *y, const float *targ
 int launch_mlp_wgrad_tc(const __nv_bfloat16 *X, const float *z1, const float *d1, const float *d2, int n, float *partial,
                         float *gW1, float *gW2, cudaStream_t s);
 void launch_fin_frozen(const Dev &d, cudaStream_t s);
+// bubble model: liquid cells, non-obstacle cells and the fixed-point fill-level
+// sum of the current state into d.bub_i (entries of the current parity and [4])
+void launch_bubble_count(const Dev &d, cudaStream_t s);
+// brick list of the current interface list (tags and the list counter reset by the caller)
+void launch_brick_build(const Dev &d, cudaStream_t s);
+// the step prologue alone (one thread), for the LSQR step whose first list kernel is the brick pass
+void launch_step_begin(const Dev &d, cudaStream_t s);
 
 int max_partials();
 // blocks of `block` threads of `kernel` that are resident on the whole GPU at once

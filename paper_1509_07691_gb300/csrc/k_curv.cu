@@ -16,37 +16,15 @@ namespace fslk {
 
 constexpr int LIST_THREADS = 128;
 
-// fill level at any cell (periodic wrap); obstacle cells take the reflection
-// reflected fill level of the obstacle cell (x, y, z); kept out of line: the
-// callers unroll over their stencils and obstacle cells are rare
-__device__ __noinline__ float phi_reflected(const Dev &d, int x, int y, int z) {
-    return reflect_value<float>([&](int a, int b, int c) { return d.flags[nbr_index(d, x, y, z, a, b, c)]; },
-                                [&](int a, int b, int c) { return d.phi[nbr_index(d, x, y, z, a, b, c)]; });
-}
-
-__device__ __forceinline__ float phi_ext(const Dev &d, int x, int y, int z) {
-    x = wrap(x, d.nx);
-    y = wrap(y, d.ny);
-    z = wrap(z, d.nz);
-    const int i = cell_index(d, x, y, z);
-    if (!(d.flags[i] & T_OBS)) return d.phi[i];
-    return phi_reflected(d, x, y, z);
-}
-
-// The first kernel of a step also zeroes that step's counters (conversion
-// lists, general-path LSQR list, FP64 re-solves, next interface list); every
-// later kernel of the step is ordered after it on the stream.
+// The first kernel of a step also runs the step prologue (counters, brick
+// tag, bubble pressure); every later kernel of the step is ordered after it on
+// the stream.
 __global__ void __launch_bounds__(LIST_THREADS) k_normals(Dev d) {
     pdl_enter();
     int cnt[1];
     block_counts<1>(d.counts, {d.cif}, cnt);
     const int n = cnt[0];
-    if (blockIdx.x == 0 && threadIdx.x == 8) d.counts[d.cif_next] = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 9) d.counts[d.cdirty_next] = 0;
-    if (blockIdx.x == 0 && threadIdx.x < 8) {
-        const int zero[8] = {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF, C_SLOW, C_FP64, C_MLP, C_MLPKEEP};
-        d.counts[zero[threadIdx.x]] = 0;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) step_prologue(d);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = d.iflist[k];
         int x, y, z;
@@ -100,6 +78,84 @@ __global__ void __launch_bounds__(LIST_THREADS) k_lsqr_slow(Dev d, float *kappa_
             atomicAdd(d.counts + C_FP64, 1);
         }
         kappa_out[i] = kap;
+    }
+}
+
+// ---- TR (Sec. II.B) -------------------------------------------------------------
+// Triangle-fan curvature of the PLIC points (Pohl's fan, Taubin's mean
+// curvature).  One warp per interface cell; lane t (0..26) holds block cell
+// t = (dz+1)*9 + (dy+1)*3 + (dx+1).  In the tangent frame of the centre
+// point (the LSQR frame), lane t takes the PLIC point of its cell if that
+// cell is interface with a nonzero normal (centre excluded) and its
+// projection is not within 1e-6 of the centre: (u, v, h), the angle
+// atan2(v, u) and the directional curvature 2h / |p|^2.  The fan orders the
+// points by (angle, t); each lane finds its successor in that cyclic order by
+// a scan over the warp, and if the angular gap is below pi the triangle
+// (centre, own point, successor) adds its surface area times the two
+// directional curvatures to the numerator and twice the area to the
+// denominator: kappa = sum / sum, the mean of the directional curvatures
+// weighted by the areas of the triangles at each edge.  No triangle: 0.
+constexpr float TR_TWO_PI = 6.28318530717958647692f;
+constexpr float TR_PI = 3.14159265358979323846f;
+
+__global__ void __launch_bounds__(LIST_THREADS) k_tr(Dev d, float *kappa_out) {
+    int cnt[1];
+    block_counts<1>(d.counts, {d.cif}, cnt);
+    const int n = cnt[0];
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const int t = lane < 27 ? lane : 13;
+    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+    for (int k = gw; k < n; k += nw) {  // warp-uniform
+        const int i = d.iflist[k];
+        int x, y, z;
+        cell_coords(d, i, x, y, z);
+        const float4 c4 = d.normal[i];
+        const bool none = c4.x == 0.f && c4.y == 0.f && c4.z == 0.f;  // warp-uniform
+        const int j = nbr_index(d, x, y, z, dx, dy, dz);
+        const uint8_t fj = d.flags[j];
+        const float4 q4 = d.normal[j];
+        FastFrame F;
+        lsqr_fast_frame(none ? make_float4(0.f, 0.f, 1.f, 0.f) : c4, F);
+        const float ex = dx + q4.w * q4.x - F.p[0], ey = dy + q4.w * q4.y - F.p[1], ez = dz + q4.w * q4.z - F.p[2];
+        const float u = ex * F.tu[0] + ey * F.tu[1] + ez * F.tu[2];
+        const float v = ex * F.tv[0] + ey * F.tv[1] + ez * F.tv[2];
+        const float h = ex * F.n[0] + ey * F.n[1] + ez * F.n[2];
+        const float r2 = u * u + v * v;
+        const bool valid = !none && lane < 27 && t != 13 && (fj & T_IF) &&
+                           !(q4.x == 0.f && q4.y == 0.f && q4.z == 0.f) && r2 >= 1e-12f;
+        const float ang = atan2f(v, u);
+        const float kap = 2.0f * h / (r2 + h * h);
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        // successor in the cyclic (angle, t) order: smallest gap, then smallest t
+        float best = 3.0e38f;
+        int succ = -1;
+#pragma unroll
+        for (int s = 0; s < 27; ++s) {
+            const float as = __shfl_sync(0xffffffffu, ang, s);
+            float g = as - ang;
+            if (g < 0.f || (g == 0.f && s < lane)) g += TR_TWO_PI;
+            if (valid && ((vmask >> s) & 1u) && s != lane && g < best) {
+                best = g;
+                succ = s;
+            }
+        }
+        const int src = succ < 0 ? lane : succ;
+        const float us = __shfl_sync(0xffffffffu, u, src), vs = __shfl_sync(0xffffffffu, v, src);
+        const float hs = __shfl_sync(0xffffffffu, h, src), ks = __shfl_sync(0xffffffffu, kap, src);
+        float num = 0.f, den = 0.f;
+        if (valid && succ >= 0 && best < TR_PI) {
+            const float cx_ = v * hs - h * vs, cy_ = h * us - u * hs, cz_ = u * vs - v * us;
+            const float area = 0.5f * sqrtf(cx_ * cx_ + cy_ * cy_ + cz_ * cz_);
+            num = area * (kap + ks);
+            den = 2.0f * area;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_xor_sync(0xffffffffu, num, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+        }
+        if (lane == 0) kappa_out[i] = den > 0.f ? num / den : 0.f;
     }
 }
 
@@ -226,6 +282,10 @@ void launch_lsqr(const Dev &d, float *kappa_out, cudaStream_t s) {
 void launch_fd(const Dev &d, float *kappa_out, cudaStream_t s) {
     static const int g = list_blocks((const void *)k_fd, LIST_THREADS, 4);
     k_fd<<<g, LIST_THREADS, 0, s>>>(d, kappa_out);
+}
+void launch_tr(const Dev &d, float *kappa_out, cudaStream_t s) {
+    static const int g = list_blocks((const void *)k_tr, LIST_THREADS, 8);
+    k_tr<<<g, LIST_THREADS, 0, s>>>(d, kappa_out);
 }
 void launch_zero_kappa(const Dev &d, float *kappa_out, cudaStream_t s) {
     static const int g = list_blocks((const void *)k_zero_kappa, LIST_THREADS, 4);

@@ -210,6 +210,81 @@ void launch_refresh(const Dev &d, cudaStream_t s) {
     k_refresh<<<grid, 256, 0, s>>>(d);
 }
 
+// ---- prescribed flow (the advection test of Sec. III.A) -------------------------
+// f' = feq(rho, u) at every liquid and interface cell of the active segments,
+// so that the next step carries the fill level along a constant flow by the
+// mass exchange alone.  One warp per 32-cell segment.
+template <int S>
+__global__ void __launch_bounds__(256) k_prescribe(Dev d, float rho, float ux, float uy, float uz) {
+    int cnt[1];
+    block_counts<1>(d.counts, {C_SEG}, cnt);
+    const int nseg = cnt[0];
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+    for (int k = gw; k < nseg; k += nw) {
+        const int s = d.seg_list[k];
+        const int row = s / d.nsegx;
+        const int x = (s - row * d.nsegx) * SEG + lane;
+        if (x >= d.nx) continue;
+        const int z = row / d.ny, y = row - z * d.ny;
+        const int i = cell_index(d, x, y, z);
+        if (!(d.flags[i] & (T_LIQ | T_IF))) continue;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+            Store<S>::st(d.fdst, (long long)q * d.N + i, q, wq(q) * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - uu), d);
+        }
+    }
+}
+
+void launch_prescribe(const Dev &d, float rho, float ux, float uy, float uz, cudaStream_t s) {
+    static const int g = resident_grid((const void *)k_prescribe<FSL_F32>, 256);
+    switch (d.storage) {
+    case FSL_F32: k_prescribe<FSL_F32><<<g, 256, 0, s>>>(d, rho, ux, uy, uz); break;
+    case FSL_F16_OFS: k_prescribe<FSL_F16_OFS><<<g, 256, 0, s>>>(d, rho, ux, uy, uz); break;
+    default: k_prescribe<FSL_BF16_OFS><<<g, 256, 0, s>>>(d, rho, ux, uy, uz); break;
+    }
+}
+
+// ---- bubble model: liquid cells, non-obstacle cells, fixed-point fill-level sum ----
+// of the current state (the entries of the current list parity and [4]; the
+// caller zeroes them first).  Block partials, one integer atomic per block and
+// quantity, so the totals do not depend on the order of the additions.
+__global__ void __launch_bounds__(256) k_bubble_count(Dev d) {
+    long long nl = 0, no = 0, sp = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.N; i += (long long)gridDim.x * blockDim.x) {
+        const uint8_t t = d.flags[i] & T_MASK;
+        nl += t == T_LIQ;
+        no += t != T_OBS;
+        if (t == T_IF) sp += __double2ll_rn((double)d.phi[i] * BUB_FIX);
+    }
+    __shared__ long long red[3][8];
+    for (int o = 16; o > 0; o >>= 1) {
+        nl += __shfl_down_sync(0xffffffffu, nl, o);
+        no += __shfl_down_sync(0xffffffffu, no, o);
+        sp += __shfl_down_sync(0xffffffffu, sp, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = nl;
+        red[1][threadIdx.x >> 5] = no;
+        red[2][threadIdx.x >> 5] = sp;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        long long t = 0;
+        for (int w = 0; w < 8; ++w) t += red[threadIdx.x][w];
+        const int par = list_parity(d);
+        const int slot = threadIdx.x == 0 ? par : (threadIdx.x == 1 ? 4 : 2 + par);
+        if (t) atomicAdd(reinterpret_cast<unsigned long long *>(d.bub_i + slot), (unsigned long long)t);
+    }
+}
+
+void launch_bubble_count(const Dev &d, cudaStream_t s) {
+    static const int g = resident_grid((const void *)k_bubble_count, 256);
+    k_bubble_count<<<g, 256, 0, s>>>(d);
+}
+
 // ---- statistics ----------------------------------------------------------------
 // stats[0..5]: liquid, interface, gas, obstacle, interface without liquid or gas
 // neighbour, liquid touching gas.  One atomic per block and counter.

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfsl.so")
 OK, EINVAL, ECUDA, ECAPACITY, ETIMEOUT, ENAN, EUNSUPPORTED, EIO = 0, -1, -2, -3, -4, -5, -6, -7
 LIQUID, INTERFACE, GAS, OBSTACLE, TYPE_MASK, NEAR_OBSTACLE = 1, 2, 4, 8, 15, 16
 BGK, TRT = 0, 1
-CURV_LSQR, CURV_FD, CURV_NONE, CURV_MLP = 0, 1, 2, 3
+CURV_LSQR, CURV_FD, CURV_NONE, CURV_MLP, CURV_TR = 0, 1, 2, 3, 4
 F32, F16_OFS, BF16_OFS = 0, 1, 2
 WHERE_NONE, WHERE_HOST, WHERE_DEVICE = 0, 1, 2
 JAC_STRIDE = 344  # curvature Jacobian row: 7x7x7 window slots, then theta
@@ -35,7 +35,7 @@ class Params(ctypes.Structure):
                 ("storage_shift", ctypes.c_int32), ("plic_iters", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("magic", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("p_gas", ctypes.c_double), ("theta", ctypes.c_double), ("eps_convert", ctypes.c_double),
-                ("lsqr_fp64_cond", ctypes.c_double)]
+                ("lsqr_fp64_cond", ctypes.c_double), ("excess_rule", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class Fields(ctypes.Structure):
@@ -66,6 +66,11 @@ _SIGNATURES = {
     "fsl_mass": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "fsl_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "fsl_step_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    "fsl_prescribe_flow": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_double] * 4),
+    "fsl_set_bubble": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]),
+    "fsl_bubble": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "fsl_conversions": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p,
+                                       ctypes.c_int64]),
     "fsl_mass_static": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "fsl_mlp_param_bytes": (ctypes.c_size_t, []),
@@ -128,11 +133,11 @@ def check(rc: int, what: str = ""):
 
 def make_params(shape, collision=BGK, curv_model=CURV_LSQR, storage=F32, storage_shift=8, plic_iters=4, tau=1.0,
                 magic=3.0 / 16.0, sigma=0.0, p_gas=1.0 / 3.0, theta=math.pi / 2, eps_convert=1e-3,
-                lsqr_fp64_cond=1e6) -> Params:
+                lsqr_fp64_cond=1e6, excess_rule=0) -> Params:
     """shape = (nz, ny, nx) of the numpy/torch arrays (x fastest)."""
     nz, ny, nx = shape
     return Params(nx, ny, nz, collision, curv_model, storage, storage_shift, plic_iters, tau, magic, sigma, p_gas,
-                  theta, eps_convert, lsqr_fp64_cond)
+                  theta, eps_convert, lsqr_fp64_cond, excess_rule, 0)
 
 
 def make_geometry(kind, c=(0, 0, 0), R=0.0, eps2=0.0, c2=(0, 0, 0), R2=0.0, zw=0.0, n=(0, 0, 1), d=0.0, h0=0.0,
@@ -228,6 +233,35 @@ class Sim:
         out = (ctypes.c_int64 * 10)()
         check(lib().fsl_stats(self.ctx, out), "fsl_stats")
         return np.array(list(out), dtype=np.int64)
+
+    def prescribe_flow(self, rho: float, u):
+        """f' = feq(rho, u) at every liquid and interface cell (fsl_prescribe_flow)."""
+        check(lib().fsl_prescribe_flow(self.ctx, float(rho), float(u[0]), float(u[1]), float(u[2])),
+              "fsl_prescribe_flow")
+
+    def set_bubble(self, p0: float, V0: float = 0.0):
+        """Bubble model on (p0 > 0; V0 <= 0: the current gas volume) or off (p0 = 0)."""
+        check(lib().fsl_set_bubble(self.ctx, float(p0), float(V0)), "fsl_set_bubble")
+
+    def bubble(self):
+        """(gas volume, gas pressure of the next step) of the bubble model."""
+        v, p = ctypes.c_double(), ctypes.c_double()
+        check(lib().fsl_bubble(self.ctx, ctypes.byref(v), ctypes.byref(p)), "fsl_bubble")
+        return v.value, p.value
+
+    def conversions(self):
+        """Sorted cell indices filled, emptied, new interface from gas and new
+        interface from liquid in the last step (fsl_conversions)."""
+        cnt = (ctypes.c_int64 * 4)()
+        check(lib().fsl_conversions(self.ctx, cnt, None, 0), "fsl_conversions")
+        total = int(sum(cnt))
+        cells = np.zeros(max(total, 1), dtype=np.int32)
+        check(lib().fsl_conversions(self.ctx, cnt, ctypes.c_void_p(cells.ctypes.data), total), "fsl_conversions")
+        out, o = [], 0
+        for k in range(4):
+            out.append(cells[o: o + cnt[k]].copy())
+            o += cnt[k]
+        return out
 
     def mass_static(self, out: torch.Tensor) -> int:
         """fsl_mass_static on the current state into `out` (one float64 on the

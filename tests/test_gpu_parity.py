@@ -287,13 +287,15 @@ def test_single_step_parity_reduced_precision(orc, fsl, storage, tol_f):
 
 
 @pytest.mark.parametrize("storage,tol_f", [(1, 1e-5), (2, 6e-5)])
-@pytest.mark.parametrize("nx", [70, 71])
+@pytest.mark.parametrize("nx", [70, 71, 128])
 def test_reduced_precision_pool_spans_and_x_wrap(orc, fsl, storage, tol_f, nx):
     """16-bit storage on a wavy pool between two walls that fills the whole x
     range: liquid cells at x = 0 and x = nx - 1 pull across the periodic x
     boundary, and the x rows end in a partial 32-cell segment (6 or 7 cells).
-    One step against the oracle from the decoded stored state, tolerances as
-    above."""
+    With nx = 128 (a multiple of 8) the liquid pass stages the source rows of
+    the interior segments (x0 = 32, 64) by bulk copies, the edge segments by
+    plain loads.  One step against the oracle from the decoded stored state,
+    tolerances as above."""
     import copy
     shape = (16, 12, nx)
     phi = orc.fill(orc.geom("pool", h0=8.3, amp=1.2, wavelength=nx / 2.0, sub=8), shape)

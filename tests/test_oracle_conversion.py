@@ -155,3 +155,55 @@ def test_new_cells_take_the_equilibrium_of_their_fluid_neighbours(orc):
         a = _at(c, d)
         assert nxt.flags[a] == IF
         assert np.max(np.abs(nxt.f[(slice(None),) + a] - fe)) < 1e-15
+
+
+def test_normal_weighted_excess_of_a_filling_cell(orc):
+    """Reading K1 (Koerner's normal-weighted shares): the plane's normal points
+    down into the liquid, n = (0, 0, -1); a filled cell gives with weights
+    max(0, -n.c) = max(0, c_z): the 5 new cells above (c_z = 1) get 1/5 of the
+    excess each, the 8 in-plane receivers (c_z = 0) nothing."""
+    P, st = _plane_state(orc)
+    P.excess_rule = 1
+    c = (3, 2, 2)
+    _set_mass(st, c, 1.01)
+    nxt, counts, _, _ = orc.step(P, st)
+    assert list(counts[3:7]) == [1, 0, 5, 0]
+    for d in ABOVE:
+        assert abs(nxt.mass[_at(c, d)] - 0.01 / 5) < 1e-15
+    for d in PLANE:
+        assert abs(nxt.mass[_at(c, d)] - 0.5) < 1e-15
+    assert abs(orc.mass(P, nxt) + nxt.lost - orc.mass(P, st)) < 1e-13
+
+
+def test_normal_weighted_excess_of_an_emptying_cell(orc):
+    """An emptied cell (m = -0.01) gives with weights max(0, n.c) = max(0, -c_z):
+    its negative excess goes in fifths to the 5 liquid cells below, which
+    become interface with m = rho = 1; the in-plane cells keep 0.5."""
+    P, st = _plane_state(orc)
+    P.excess_rule = 1
+    c = (3, 2, 2)
+    _set_mass(st, c, -0.01)
+    nxt, counts, _, _ = orc.step(P, st)
+    assert list(counts[3:7]) == [0, 1, 0, 5]
+    for d in BELOW:
+        a = _at(c, d)
+        assert nxt.flags[a] == IF and abs(nxt.mass[a] - (1.0 - 0.01 / 5)) < 1e-15
+    for d in PLANE:
+        assert abs(nxt.mass[_at(c, d)] - 0.5) < 1e-15
+
+
+def test_normal_weighted_rule_falls_back_to_equal_shares(orc):
+    """A filled cell whose gas-side neighbours are not interface after the
+    conversion would give zero weight to every receiver: equal shares then.
+    Here the neighbours above are obstacle cells (no new interface cells), so
+    the 8 in-plane cells take 1/8 each."""
+    P, st = _plane_state(orc)
+    P.excess_rule = 1
+    st.flags[4] = 8  # obstacle layer above the plane
+    st.phi[4] = 0.0
+    c = (3, 2, 2)
+    _set_mass(st, c, 1.01)
+    nxt, counts, _, _ = orc.step(P, st)
+    assert counts[3] == 1 and counts[5] == 0
+    for d in PLANE:
+        assert abs(nxt.mass[_at(c, d)] - (0.5 + 0.01 / 8)) < 1e-14
