@@ -42,13 +42,10 @@ size_t up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
     size_t normal, rho, excess, exw, rmark, iflist0, iflist1, fill, empty, newgas, liq2if, slow, seg_active, seg_list, counts,
-        lost, status, partial, stats, mass_out, bubble, brick0, brick1, brick_tag, total;
+        lost, status, partial, stats, mass_out, bubble, total;
 };
 
 size_t nseg_of(const fsl_params &p) { return (size_t)((p.nx + SEG - 1) / SEG) * p.ny * p.nz; }
-size_t nbrick_of(const fsl_params &p) {
-    return (size_t)((p.nx + BRK - 1) / BRK) * ((p.ny + BRK - 1) / BRK) * ((p.nz + BRK - 1) / BRK);
-}
 
 Layout layout(const fsl_params &p) {
     const size_t N = (size_t)p.nx * p.ny * p.nz;
@@ -75,9 +72,6 @@ Layout layout(const fsl_params &p) {
     L.stats = o; o += up(16 * sizeof(long long));
     L.mass_out = o; o += up(2 * sizeof(double));
     L.bubble = o; o += up(8 * sizeof(long long) + 2 * sizeof(double) + sizeof(float));
-    L.brick0 = o; o += up(nbrick_of(p) * sizeof(int));
-    L.brick1 = o; o += up(nbrick_of(p) * sizeof(int));
-    L.brick_tag = o; o += up(nbrick_of(p) * sizeof(int));
     L.total = o;
     return L;
 }
@@ -127,17 +121,11 @@ Dev make_dev(const fsl_params &p, const fsl_fields &f) {
     d.seg_list = reinterpret_cast<int *>(ws + L.seg_list);
     d.nsegx = (p.nx + SEG - 1) / SEG;
     d.nseg = (int)nseg_of(p);
-    d.nbx = (p.nx + BRK - 1) / BRK;
-    d.nby = (p.ny + BRK - 1) / BRK;
-    d.nbz = (p.nz + BRK - 1) / BRK;
-    d.brick_tag = reinterpret_cast<int *>(ws + L.brick_tag);
     // counter slots of list parity 0 (dev_for and the window view set their own)
     d.cif = C_IF0;
     d.cif_next = C_IF1;
     d.cdirty = C_SEGD0;
     d.cdirty_next = C_SEGD1;
-    d.cbrk = C_BRK0;
-    d.cbrk_next = C_BRK1;
     d.fill = reinterpret_cast<int *>(ws + L.fill);
     d.empty = reinterpret_cast<int *>(ws + L.empty);
     d.newgas = reinterpret_cast<int *>(ws + L.newgas);
@@ -184,11 +172,6 @@ Dev dev_for(const fsl_ctx *c, int parity) {
     d.cif_next = C_IF0 + (parity ^ 1);
     d.cdirty = C_SEGD0 + parity;
     d.cdirty_next = C_SEGD0 + (parity ^ 1);
-    int *bricks[2] = {reinterpret_cast<int *>(ws + L.brick0), reinterpret_cast<int *>(ws + L.brick1)};
-    d.brick_list = bricks[parity];
-    d.brick_list_next = bricks[parity ^ 1];
-    d.cbrk = C_BRK0 + parity;
-    d.cbrk_next = C_BRK0 + (parity ^ 1);
     return d;
 }
 
@@ -219,8 +202,8 @@ int enqueue_step_graph(const fsl_ctx *c, int parity) {
     launch_sc_bulk(d, side);
     CK(cudaEventRecord(c->join, side));
     if (c->p.curv_model == FSL_CURV_LSQR) {
-        launch_step_begin(d, s);
-        launch_curv_iface(d, s);  // normals, fit and interface stream-collide per brick
+        launch_normals(d, s);
+        launch_curv_iface(d, s);
     } else {
         enqueue_curvature(d, c->p.curv_model, d.kappa, s);
         launch_sc_iface(d, s);
@@ -315,10 +298,6 @@ Dev window_dev(const fsl_ctx *c, char *ws, const AdjLayout &A) {
     d.cif_next = C_IF1;
     d.cdirty = C_SEGD0;
     d.cdirty_next = C_SEGD1;
-    d.cbrk = C_BRK0;  // no brick list in a window: the frozen step runs the list kernels
-    d.cbrk_next = C_BRK1;
-    d.brick_list = nullptr;
-    d.brick_list_next = nullptr;
     d.seg_list = reinterpret_cast<int *>(ws + A.wseg);
     d.frozen = 1;
     return d;
@@ -448,8 +427,6 @@ int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *ph
         d0.fdst = fields->f[0];
         launch_init_state(d0, fields->flags[1], s);
         launch_seg_compact(d0, s);
-        if (cudaMemsetAsync(c->base.brick_tag, 0xff, nbrick_of(c->p) * sizeof(int), s) != cudaSuccess) break;
-        launch_brick_build(d0, s);
         // the second buffer starts as a copy, so every cell of both buffers
         // holds a defined value (w_q away from the fluid) from here on
         const size_t fbytes = (size_t)Q * N * pdf_elem_bytes(c->p.storage);
@@ -475,8 +452,6 @@ int fsl_refresh(fsl_ctx *c) {
     CK(cudaMemsetAsync(d.rmark, 0, d.N, c->stream));
     launch_refresh(d, c->stream);
     launch_seg_compact(d, c->stream);
-    CK(cudaMemsetAsync(d.brick_tag, 0xff, nbrick_of(c->p) * sizeof(int), c->stream));
-    launch_brick_build(d, c->stream);
     if (c->bubble) {  // the caller may have changed the liquid volume: recount it
         CK(cudaMemsetAsync(c->base.bub_i, 0, 5 * sizeof(long long), c->stream));
         launch_bubble_count(d, c->stream);
@@ -510,10 +485,9 @@ int fsl_step_profile(fsl_ctx *c, float ms_out[6]) {
     int rc = FSL_ECUDA;
     do {
         if (cudaEventRecord(ev[0], s) != cudaSuccess) break;
-        const bool fused = c->p.curv_model == FSL_CURV_LSQR;
-        if (fused) launch_step_begin(d, s);  // the normals are part of the brick pass
-        else launch_normals(d, s);
+        launch_normals(d, s);
         if (cudaEventRecord(ev[1], s) != cudaSuccess) break;
+        const bool fused = c->p.curv_model == FSL_CURV_LSQR;
         if (fused) launch_curv_iface(d, s);  // curvature + interface stream-collide
         else if (c->p.curv_model == FSL_CURV_MLP) launch_lsqr(d, d.kappa, s);
         else if (c->p.curv_model == FSL_CURV_FD) launch_fd(d, d.kappa, s);

@@ -49,14 +49,8 @@ enum : uint8_t {
 // buffers, conversion lists, FP64 LSQR re-solves, active segments, and the
 // two "segment set changed" flags (one per step parity: a step sets its own,
 // clears the next step's, and rebuilds the segment list only if it is set)
-// (C_BRK0/1: lengths of the two brick lists; C_TAG: step tag of the brick marks)
 enum { C_IF0 = 0, C_IF1 = 1, C_FILL = 2, C_EMPTY = 3, C_NEWGAS = 4, C_LIQ2IF = 5, C_FP64 = 6, C_SEG = 7, C_SLOW = 8,
-       C_MLP = 9, C_MLPKEEP = 10, C_ADJ64 = 11, C_SEGD0 = 12, C_SEGD1 = 13, C_BRK0 = 14, C_BRK1 = 15, C_TAG = 16,
-       C_NCOUNT = 20 };
-
-// bricks of BRK^3 cells: the LSQR step's interface pass runs one block per
-// brick that holds interface cells
-constexpr int BRK = 8;
+       C_MLP = 9, C_MLPKEEP = 10, C_ADJ64 = 11, C_SEGD0 = 12, C_SEGD1 = 13, C_NCOUNT = 16 };
 
 // the grid is walked in x-row segments of SEG cells (one warp each); a
 // segment is active while it holds a liquid or interface cell
@@ -116,12 +110,6 @@ struct Dev {
     uint8_t *rmark;    // 1: the cell receives excess mass in this step's final update (0 between steps)
     int *seg_list;
     int nsegx, nseg;
-    // bricks holding interface cells at t and at t+1 (built by the final update),
-    // their counters, and the per-brick tag of the step that listed it last
-    int *brick_list, *brick_list_next;
-    int cbrk, cbrk_next;
-    int *brick_tag;
-    int nbx, nby, nbz;
     int *counts;
     double *lost;
     int *status;
@@ -167,24 +155,18 @@ __device__ __forceinline__ float excess_weight(const float4 n, bool filled, int 
 // list parity of the step that d describes (0 or 1)
 __device__ __forceinline__ int list_parity(const Dev &d) { return d.cif - C_IF0; }
 
-__device__ __forceinline__ int brick_of(const Dev &d, int x, int y, int z) {
-    return x / BRK + d.nbx * (y / BRK + d.nby * (z / BRK));
-}
-
 // Work at the start of a step (or of a curvature pass), by one thread, before
 // any kernel of the step appends to a list: zero the step's counters and the
-// counters of the lists the final update builds, advance the brick tag, and
-// with the bubble model set this step's gas density 3 p_g = 3 p0 V0 / V from
-// the gas volume V = non-obstacle cells - liquid cells - interface fill levels
-// of the state the step starts from.
+// counter of the list the final update builds, and with the bubble model set
+// this step's gas density 3 p_g = 3 p0 V0 / V from the gas volume V =
+// non-obstacle cells - liquid cells - interface fill levels of the state the
+// step starts from.
 __device__ __forceinline__ void step_prologue(const Dev &d) {
     const int zero[8] = {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF, C_SLOW, C_FP64, C_MLP, C_MLPKEEP};
 #pragma unroll
     for (int k = 0; k < 8; ++k) d.counts[zero[k]] = 0;
     d.counts[d.cif_next] = 0;
     d.counts[d.cdirty_next] = 0;
-    d.counts[d.cbrk_next] = 0;
-    d.counts[C_TAG] += 1;
     if (d.bub_i) {
         const int par = list_parity(d);
         const double V = (double)(d.bub_i[4] - d.bub_i[par]) - (double)d.bub_i[2 + par] / BUB_FIX;
@@ -356,10 +338,7 @@ void launch_fin_frozen(const Dev &d, cudaStream_t s);
 // bubble model: liquid cells, non-obstacle cells and the fixed-point fill-level
 // sum of the current state into d.bub_i (entries of the current parity and [4])
 void launch_bubble_count(const Dev &d, cudaStream_t s);
-// brick list of the current interface list (tags and the list counter reset by the caller)
-void launch_brick_build(const Dev &d, cudaStream_t s);
-// the step prologue alone (one thread), for the LSQR step whose first list kernel is the brick pass
-void launch_step_begin(const Dev &d, cudaStream_t s);
+
 
 int max_partials();
 // blocks of `block` threads of `kernel` that are resident on the whole GPU at once

@@ -149,15 +149,11 @@ void launch_window_finish(const Dev &dst, const int *wcounts, const int *wlist, 
     k_window_finish<<<g, 256, 0, s>>>(dst, wcounts, wlist);
 }
 
-// A step with frozen types over the window's own interface list: normals,
-// curvature and the interface stream-collide as list kernels (the window has
-// no brick list; the forward pass and its recomputation both take this path).
 void launch_frozen_step(const Dev &d, cudaStream_t s) {
     launch_normals(d, s);
     launch_sc_bulk(d, s);
     if (d.curv_model == FSL_CURV_LSQR) {
-        launch_lsqr(d, d.kappa, s);
-        launch_sc_iface(d, s);
+        launch_curv_iface(d, s);
     } else {
         launch_zero_kappa(d, d.kappa, s);
         launch_sc_iface(d, s);

@@ -16,9 +16,8 @@ namespace fslk {
 
 constexpr int LIST_THREADS = 128;
 
-// The first kernel of a step also runs the step prologue (counters, brick
-// tag, bubble pressure); every later kernel of the step is ordered after it on
-// the stream.
+// The first kernel of a step also runs the step prologue (counters, bubble
+// pressure); every later kernel of the step is ordered after it on the stream.
 __global__ void __launch_bounds__(LIST_THREADS) k_normals(Dev d) {
     pdl_enter();
     int cnt[1];
@@ -262,6 +261,92 @@ __global__ void __launch_bounds__(LIST_THREADS) k_fd(Dev d, float *kappa_out) {
     }
 }
 
+// FD curvature, one warp per interface cell: the fill levels of the 7^3
+// block around the cell are staged in shared memory once, the lanes share the
+// 5^3 K8-smoothed values, six lanes take the face neighbours' normals and
+// lane 0 the central differences.  The sums run in the order of smooth_at,
+// parker_youngs and k_fd, so the values are those of the per-cell path; a
+// cell with an obstacle in its 7^3 block (reflected fill levels and wetting
+// normals) takes that path (fd_normal) on lane 0.
+constexpr int FD_WARPS = 4;
+
+// the per-cell path (walls in reach), out of line so that its registers do not
+// weigh on the staged path
+__device__ __noinline__ float fd_cell(const Dev &d, int x, int y, int z) {
+    float np[3], nm[3], div = 0.f;
+    fd_normal(d, x + 1, y, z, np);
+    fd_normal(d, x - 1, y, z, nm);
+    div += np[0] - nm[0];
+    fd_normal(d, x, y + 1, z, np);
+    fd_normal(d, x, y - 1, z, nm);
+    div += np[1] - nm[1];
+    fd_normal(d, x, y, z + 1, np);
+    fd_normal(d, x, y, z - 1, nm);
+    div += np[2] - nm[2];
+    return -0.25f * div;
+}
+
+__global__ void __launch_bounds__(32 * FD_WARPS) k_fd_warp(Dev d, float *kappa_out) {
+    __shared__ float s_phi[FD_WARPS][343];
+    __shared__ float s_sm[FD_WARPS][125];
+    __shared__ float s_n[FD_WARPS][6][3];
+    int cnt[1];
+    block_counts<1>(d.counts, {d.cif}, cnt);
+    const int n = cnt[0];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
+    float *ph = s_phi[w], *sm = s_sm[w];
+    for (int k = gw; k < n; k += nw) {  // warp-uniform
+        const int i = d.iflist[k];
+        int x, y, z;
+        cell_coords(d, i, x, y, z);
+        bool obs = false;
+        for (int e = lane; e < 343; e += 32) {
+            const int j = nbr_index(d, x, y, z, e % 7 - 3, (e / 7) % 7 - 3, e / 49 - 3);
+            obs |= (d.flags[j] & T_OBS) != 0;
+            ph[e] = d.phi[j];
+        }
+        if (__any_sync(0xffffffffu, obs)) {  // walls in reach: the per-cell path
+            if (lane == 0) kappa_out[i] = fd_cell(d, x, y, z);
+            __syncwarp();
+            continue;
+        }
+        __syncwarp();
+        // smoothed fill level of the 5^3 block (offsets -2..2), as smooth_at
+        for (int e = lane; e < 125; e += 32) {
+            const int ex = e % 5 + 1, ey = (e / 5) % 5 + 1, ez = e / 25 + 1;  // in the 7^3 block
+            float acc = 0.f;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx)
+                        acc += k8w(dx, dy, dz) * ph[(ez + dz) * 49 + (ey + dy) * 7 + ex + dx];
+            sm[e] = acc * (1.0f / 3.6796875f);
+        }
+        __syncwarp();
+        // normals at the face neighbours x+e_x, x-e_x, x+e_y, x-e_y, x+e_z, x-e_z
+        if (lane < 6) {
+            const int ax = lane >> 1, sg = (lane & 1) ? -1 : 1;
+            const int cxn = 2 + (ax == 0 ? sg : 0), cyn = 2 + (ax == 1 ? sg : 0), czn = 2 + (ax == 2 ? sg : 0);
+            float nv[3];
+            parker_youngs<float>(
+                [&](int dx, int dy, int dz) { return sm[(czn + dz) * 25 + (cyn + dy) * 5 + cxn + dx]; }, nv);
+            unit_or_zero(nv);
+            s_n[w][lane][0] = nv[0];
+            s_n[w][lane][1] = nv[1];
+            s_n[w][lane][2] = nv[2];
+        }
+        __syncwarp();
+        if (lane == 0) {
+            float div = 0.f;
+            div += s_n[w][0][0] - s_n[w][1][0];
+            div += s_n[w][2][1] - s_n[w][3][1];
+            div += s_n[w][4][2] - s_n[w][5][2];
+            kappa_out[i] = -0.25f * div;
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void k_zero_kappa(Dev d, float *kappa_out) {
     int cnt[1];
     block_counts<1>(d.counts, {d.cif}, cnt);
@@ -280,8 +365,8 @@ void launch_lsqr(const Dev &d, float *kappa_out, cudaStream_t s) {
     k_lsqr_slow<<<gs, LIST_THREADS, 0, s>>>(d, kappa_out);
 }
 void launch_fd(const Dev &d, float *kappa_out, cudaStream_t s) {
-    static const int g = list_blocks((const void *)k_fd, LIST_THREADS, 4);
-    k_fd<<<g, LIST_THREADS, 0, s>>>(d, kappa_out);
+    static const int g = list_blocks((const void *)k_fd_warp, 32 * FD_WARPS, 16);
+    k_fd_warp<<<g, 32 * FD_WARPS, 0, s>>>(d, kappa_out);
 }
 void launch_tr(const Dev &d, float *kappa_out, cudaStream_t s) {
     static const int g = list_blocks((const void *)k_tr, LIST_THREADS, 8);

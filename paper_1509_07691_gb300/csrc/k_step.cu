@@ -4,12 +4,10 @@
 // interface list and of the active segments for the next step.
 //
 // Work decomposition: liquid cells are processed by k_sc_bulk over the active
-// x-row segments (coalesced SoA loads, one thread per cell); interface cells,
-// with the LSQR model, by k_brick over the bricks holding them (normals, fit
-// and stream-collide from fill levels and normals staged in shared memory),
-// with the other models by k_sc_iface over the interface list; everything
-// after the collision only touches list entries, so no pass sweeps the whole
-// grid.
+// x-row segments (coalesced SoA loads, one thread per cell); interface cells
+// by k_curv_iface_fast (LSQR model, fit and stream-collide fused) or
+// k_sc_iface (other models) over the interface list; everything after the
+// collision only touches list entries, so no pass sweeps the whole grid.
 #include "curv_common.cuh"
 
 namespace fslk {
@@ -112,177 +110,6 @@ __global__ void __launch_bounds__(256) k_sc_bulk(Dev d) {
             d.seg_active[s] = 0;
             d.counts[d.cdirty] = 1;
         }
-    }
-}
-
-// ---- liquid cells with 16-bit offset storage: source rows staged by bulk copies --
-// The 16-bit pass moves half the bytes of the FP32 one, but with one 2-byte
-// load per lane and direction it issues as many load instructions and needs
-// as many in flight.  Here lane 0 of each warp stages the 19 source rows of a
-// 32-cell segment in shared memory with bulk asynchronous copies (one 96-byte
-// copy per direction: elements x0 - 8 .. x0 + 39 of the row at (y - c_y,
-// z - c_z), which holds x0 - c_x + lane for every lane), completing on an
-// mbarrier; the lanes then read their shifted values from shared memory.
-// Three stages per warp keep the next segments' rows in flight while one is
-// computed.  Segments whose window would leave the row (x0 < 8 or x0 + 40 >
-// nx) take the plain loads; the host uses this kernel only when nx is a
-// multiple of 8 (16-byte aligned rows).  Every mbarrier wait is bounded: if
-// one runs out the kernel records FSL_ETIMEOUT in the status word, waits (again
-// bounded) for its copies still in flight and leaves the segment unwritten.
-constexpr int B16_STAGES = 3, B16_ROW = 48, B16_OFF = 8;
-constexpr int B16_ROW_BYTES = B16_ROW * 2;  // 96: a multiple of 16
-constexpr long long B16_WAIT = 1ll << 22;
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool b16_wait(unsigned long long *bar, uint32_t parity) {
-    const uint32_t a = smem_addr(bar);
-    for (long long it = 0; it < B16_WAIT; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// lane 0: stage the 19 source rows of segment (x0, y, z) into buf (19 x B16_ROW)
-template <int S>
-__device__ __forceinline__ void b16_issue(const Dev &d, int x0, int y, int z, uint16_t *buf, unsigned long long *bar) {
-    const uint32_t b = smem_addr(bar);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of buf before the async writes
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(Q * B16_ROW_BYTES) : "memory");
-    const uint16_t *src = static_cast<const uint16_t *>(d.fsrc);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int ys = wrap(y - cy(q), d.ny), zs = wrap(z - cz(q), d.nz);
-        const uint16_t *g = src + (long long)q * d.N + cell_index(d, x0 - B16_OFF, ys, zs);
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_addr(buf + q * B16_ROW)),
-            "l"(g), "r"(B16_ROW_BYTES), "r"(b)
-            : "memory");
-    }
-}
-
-template <int S>
-__device__ __forceinline__ float b16_decode(uint16_t v, int q, const Dev &d) {
-    if (S == FSL_F16_OFS) return fmaf(__half2float(__ushort_as_half(v)), d.inv_scale, wq(q));
-    return fmaf(__bfloat162float(__ushort_as_bfloat16(v)), d.inv_scale, wq(q));
-}
-
-template <int S, int COLL>
-__global__ void __launch_bounds__(256) k_sc_bulk16(Dev d) {
-    using St = Store<S>;
-    __shared__ __align__(16) uint16_t s_rows[8][B16_STAGES][Q * B16_ROW];
-    __shared__ __align__(8) unsigned long long s_bar[8][B16_STAGES];
-    int cnt[1];
-    block_counts<1>(d.counts, {C_SEG}, cnt);
-    const int nseg = cnt[0];
-    const long long N = d.N;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
-    if (lane == 0)
-        for (int st = 0; st < B16_STAGES; ++st)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar[wib][st])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    __syncwarp();
-    uint32_t phase = 0;     // bit st: parity of stage st's next completion
-    uint32_t inflight = 0;  // bit st: stage st has copies issued and not yet waited for
-    bool failed = false;    // warp-uniform
-    auto seg_xyz = [&](int k, int &x0, int &y, int &z) {
-        const int s = d.seg_list[k];
-        const int row = s / d.nsegx;
-        x0 = (s - row * d.nsegx) * SEG;
-        z = row / d.ny;
-        y = row - z * d.ny;
-    };
-    auto staged = [&](int x0) { return x0 >= B16_OFF && x0 + B16_ROW - B16_OFF <= d.nx; };
-    // prologue: stage the first segments
-#pragma unroll
-    for (int st = 0; st < B16_STAGES; ++st) {
-        const int k = gw + st * nw;
-        if (k < nseg) {
-            int x0, y, z;
-            seg_xyz(k, x0, y, z);
-            if (staged(x0)) {
-                if (lane == 0) b16_issue<S>(d, x0, y, z, s_rows[wib][st], &s_bar[wib][st]);
-                inflight |= 1u << st;
-            }
-        }
-    }
-    int st = 0;
-    for (int k = gw; k < nseg; k += nw) {
-        int x0, y, z;
-        seg_xyz(k, x0, y, z);
-        const bool use = staged(x0);  // warp-uniform
-        if (use && !failed) {
-            const bool ok = __all_sync(0xffffffffu, b16_wait(&s_bar[wib][st], (phase >> st) & 1u));
-            if (ok) {
-                phase ^= 1u << st;
-                inflight &= ~(1u << st);
-            } else {
-                failed = true;
-            }
-        }
-        const int x = x0 + lane;
-        const bool inb = x < d.nx;
-        const int i = inb ? cell_index(d, x, y, z) : 0;
-        const uint8_t fl = inb ? d.flags[i] : (uint8_t)T_GAS;
-        if ((fl & T_LIQ) && !(use && failed)) {
-            float f[Q];
-            if (use) {
-                const uint16_t *rows = s_rows[wib][st];
-#pragma unroll
-                for (int q = 0; q < Q; ++q) f[q] = b16_decode<S>(rows[q * B16_ROW + B16_OFF + lane - cx(q)], q, d);
-                if (fl & B_NEAR) {
-                    int src[Q];
-                    sources(d, x, y, z, src);
-#pragma unroll
-                    for (int q = 1; q < Q; ++q)
-                        if (d.flags[src[q]] & T_OBS) f[q] = St::ld(d.fsrc, (long long)opp(q) * N + i, opp(q), d);
-                }
-            } else {
-                int src[Q];
-                sources(d, x, y, z, src);
-                f[0] = St::ld(d.fsrc, i, 0, d);
-#pragma unroll
-                for (int q = 1; q < Q; ++q) {
-                    const bool wall = (fl & B_NEAR) && (d.flags[src[q]] & T_OBS) != 0;
-                    f[q] = wall ? St::ld(d.fsrc, (long long)opp(q) * N + i, opp(q), d)
-                                : St::ld(d.fsrc, (long long)q * N + src[q], q, d);
-                }
-            }
-            float rho;
-            collide<COLL>(f, d, rho);
-#pragma unroll
-            for (int q = 0; q < Q; ++q) St::st(d.fdst, (long long)q * N + i, q, f[q], d);
-        }
-        if (!__any_sync(0xffffffffu, (fl & (T_LIQ | T_IF)) != 0) && lane == 0) {
-            d.seg_active[d.seg_list[k]] = 0;
-            d.counts[d.cdirty] = 1;
-        }
-        __syncwarp();  // every lane is done with this stage's rows
-        // refill this stage with the segment STAGES turns ahead
-        const int kn = k + B16_STAGES * nw;
-        if (kn < nseg && !failed) {
-            int xn, yn, zn;
-            seg_xyz(kn, xn, yn, zn);
-            if (staged(xn)) {
-                if (lane == 0) b16_issue<S>(d, xn, yn, zn, s_rows[wib][st], &s_bar[wib][st]);
-                inflight |= 1u << st;
-            }
-        }
-        st = st + 1 == B16_STAGES ? 0 : st + 1;
-    }
-    if (failed) {
-        // drain: wait (bounded) for the copies still in flight before the block exits
-        if (lane == 0) set_status(d.status, FSL_ETIMEOUT);
-        for (int s2 = 0; s2 < B16_STAGES; ++s2)
-            if ((inflight >> s2) & 1u) b16_wait(&s_bar[wib][s2], (phase >> s2) & 1u);
     }
 }
 
@@ -402,12 +229,12 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_sc_iface(Dev d) {
 }
 
 // ---- LSQR curvature fused with the interface stream-collide ----------------------
-// With the LSQR model the normals, the curvature of a cell and its
-// stream-collide run in one pass per brick (k_brick, below): the FP32
-// normal-equation fit (as k_lsqr_fast) and, unless the fit defers the cell to
-// the general path, the cell's stream-collide, four lanes per cell;
-// k_curv_iface_slow finishes the deferred cells one thread each (Givens fit,
-// FP64 re-solve when ill conditioned, then iface_cell).
+// With the LSQR model the curvature of a cell and its stream-collide run in
+// one pass: k_curv_iface_fast fits the cell by the FP32 normal equations
+// (as k_lsqr_fast) and, unless the fit defers the cell to the general path,
+// goes straight on with the cell's stream-collide, FSL_IFACE_LANES lanes per
+// cell; k_curv_iface_slow finishes the deferred cells one thread each (Givens
+// fit, FP64 re-solve when ill conditioned, then iface_cell).
 // iface_cell of one cell changes only that cell's transient flag bits, mass,
 // rho and new PDFs, none of which a fit of another cell reads.
 // Lattice directions by pair: pair p (0..8) holds q = 2p + 1 with velocity
@@ -438,311 +265,227 @@ __device__ __forceinline__ int group_or(int v) {
     return v;
 }
 
-// ---- brick pass: normals, LSQR fit and interface stream-collide ------------------
-// The LSQR step's interface work, one block per BRK^3 brick that holds
-// interface cells (the bricks are listed by the final update of the previous
-// step, or by the refresh):
-//  1. the flags and fill levels of the brick and a 2-cell halo (BR2^3 cells)
-//     are staged in shared memory, one coalesced round of loads;
-//  2. the normal and PLIC offset of every interface cell of the brick and a
-//     1-cell halo (BR1^3 cells) are computed from the staged fill levels (a
-//     cell next to an obstacle reads the reflected fill levels from global
-//     memory) and kept in shared memory; those of the brick's own cells also
-//     go to global memory (general-path fits, conversion);
-//  3. each interface cell of the brick takes BRICK_LANES lanes: the FP32
-//     normal-equation fit from the staged normals and flags, then the cell's
-//     stream-collide as in iface_cell (PDFs from global memory, neighbour
-//     flags and fill levels from shared memory).  Cells the fit defers (contact
-//     rows, ill conditioning, too few rows) go to k_curv_iface_slow.
-// Normals and fits read the same values with the same arithmetic as
-// k_normals and iface_cell do from global memory.
-constexpr int BR1 = BRK + 2, BR2 = BRK + 4;
-constexpr int BRICK_THREADS = 256, BRICK_LANES = 4, BRICK_CELLS = BRICK_THREADS / BRICK_LANES;
-constexpr int BR1N = BR1 * BR1 * BR1, BR2N = BR2 * BR2 * BR2;
+// lanes per cell of the fused fit + stream-collide, and the blocks per SM its
+// register budget is held to (one wave of the list on a 256^3 droplet)
+#ifndef FSL_IFACE_LANES
+#define FSL_IFACE_LANES 2
+#endif
+constexpr int IFACE_MIN_BLOCKS = FSL_IFACE_LANES == 4 ? 3 : 3;
 
-__device__ __forceinline__ int wrapm(int a, int n) {
-    const int r = a % n;
-    return r < 0 ? r + n : r;
-}
-
-// Stream-collide (with the fit before it) of the brick cell k (local index in
-// the BRK^3 core) on the L lanes of its group, rank r.  Group-uniform control
-// flow; every lane of the warp reaches the list append at the end.
 template <int S, int COLL, int L>
-__device__ __forceinline__ void brick_cell(const Dev &d, int k, int x0, int y0, int z0, bool valid, int r,
-                                           const uint8_t *s_fl, const float *s_phi, const float4 *s_nrm) {
-    using St = Store<S>;
-    const long long N = d.N;
-    constexpr int RS = (27 + L - 1) / L;  // fit rows per lane
-    constexpr int PJ = (9 + L - 1) / L;   // direction pairs per lane
-    const int lx = k % BRK, ly = (k / BRK) % BRK, lz = k / (BRK * BRK);
-    const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-    const int i = cell_index(d, x, y, z);
-    const int c2 = ((lz + 2) * BR2 + ly + 2) * BR2 + lx + 2;  // staged flags / fill levels
-    const int c1 = ((lz + 1) * BR1 + ly + 1) * BR1 + lx + 1;  // staged normals
-    auto o2 = [&](int ox, int oy, int oz) { return c2 + (oz * BR2 + oy) * BR2 + ox; };
-    auto o1 = [&](int ox, int oy, int oz) { return c1 + (oz * BR1 + oy) * BR1 + ox; };
-    // global neighbour coordinates (periodic) for the PDF loads
-    const int xm = x == 0 ? d.nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? d.ny - 1 : y - 1, yp = y == d.ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? d.nz - 1 : z - 1, zp = z == d.nz - 1 ? 0 : z + 1;
-    auto px = [&](int o) { return o < 0 ? xm : (o > 0 ? xp : x); };
-    auto py = [&](int o) { return o < 0 ? ym : (o > 0 ? yp : y); };
-    auto pz = [&](int o) { return o < 0 ? zm : (o > 0 ? zp : z); };
-    // ---- the stream-collide's loads (independent of kappa), issued first
-    float fo[PJ][2], fin[PJ][2], phn[PJ][2];
-    uint8_t tq[PJ][2];
-    float fo0 = 0.f;
-#pragma unroll
-    for (int j = 0; j < PJ; ++j) {
-        const int p = r + L * j;
-        const int pp = p < 9 ? p : 0;
-        const int ex = pair_c(PAIR_CX, pp), ey = pair_c(PAIR_CY, pp), ez = pair_c(PAIR_CZ, pp);
-        const int q = 2 * pp + 1;
-        const int sq = cell_index(d, px(-ex), py(-ey), pz(-ez));  // x - c_q
-        const int sb = cell_index(d, px(ex), py(ey), pz(ez));     // x + c_q
-        fo[j][0] = St::ld(d.fsrc, (long long)q * N + i, q, d);
-        fo[j][1] = St::ld(d.fsrc, (long long)(q + 1) * N + i, q + 1, d);
-        fin[j][0] = St::ld(d.fsrc, (long long)q * N + sq, q, d);
-        fin[j][1] = St::ld(d.fsrc, (long long)(q + 1) * N + sb, q + 1, d);
-        tq[j][0] = s_fl[o2(-ex, -ey, -ez)] & T_MASK;
-        tq[j][1] = s_fl[o2(ex, ey, ez)] & T_MASK;
-        phn[j][0] = s_phi[o2(-ex, -ey, -ez)];
-        phn[j][1] = s_phi[o2(ex, ey, ez)];
-    }
-    if (r == L - 1) fo0 = St::ld(d.fsrc, i, 0, d);
-    const uint8_t fl = s_fl[c2];
-    const float phix = s_phi[c2];
-    const float4 c4 = s_nrm[c1];
-    // ---- LSQR fit (FP32 normal equations), rows split over the group
-    const bool nozero = !(c4.x == 0.f && c4.y == 0.f && c4.z == 0.f);
-    FastFrame F;
-    lsqr_fast_frame(nozero ? c4 : make_float4(0.f, 0.f, 1.f, 0.f), F);
-    float G[15], rv[5];
-#pragma unroll
-    for (int t = 0; t < 15; ++t) G[t] = 0.f;
-#pragma unroll
-    for (int t = 0; t < 5; ++t) rv[t] = 0.f;
-    int m = 0;
-    bool contact = r == 0 && (fl & B_NEAR) != 0;
-#pragma unroll
-    for (int s7 = 0; s7 < RS; ++s7) {
-        const int t = r + L * s7;
-        if (t < 27) {
-            const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = t / 9 - 1;
-            lsqr_fast_row(t, s_fl[o2(ox, oy, oz)], s_nrm[o1(ox, oy, oz)], F, G, rv, m, contact);
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < 15; ++t) G[t] = group_sum<L>(G[t]);
-#pragma unroll
-    for (int t = 0; t < 5; ++t) rv[t] = group_sum<L>(rv[t]);
-#pragma unroll
-    for (int o = 1; o < L; o <<= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
-    contact = group_or<L>(contact ? 1 : 0) != 0;
-    float kap = 0.f;
-    const bool ok = nozero ? lsqr_fast_solve(G, rv, m, contact, d.fp64_cond, kap) : true;
-    if (!nozero) kap = 0.f;
-    const bool defer = valid && !ok;
-    const bool act = valid && ok;  // group-uniform
-    // ---- interface stream-collide of the cell, direction pairs over the group
-    float r0 = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, wx = 0.f, wy = 0.f, wz = 0.f;
-    int gas = 0, obs = 0;
-#pragma unroll
-    for (int j = 0; j < PJ; ++j) {
-        const int p = r + L * j;
-        if (p < 9) {
-            const int ex = pair_c(PAIR_CX, p), ey = pair_c(PAIR_CY, p), ez = pair_c(PAIR_CZ, p);
-            r0 += fo[j][0] + fo[j][1];
-            const float dj = fo[j][0] - fo[j][1];
-            jx += ex * dj;
-            jy += ey * dj;
-            jz += ez * dj;
-            gas |= ((tq[j][0] | tq[j][1]) & T_GAS) ? 1 : 0;
-            if (tq[j][0] & T_OBS) { obs = 1; wx -= ex; wy -= ey; wz -= ez; }
-            if (tq[j][1] & T_OBS) { obs = 1; wx += ex; wy += ey; wz += ez; }
-        }
-    }
-    if (r == L - 1) r0 += fo0;
-    r0 = group_sum<L>(r0);
-    jx = group_sum<L>(jx);
-    jy = group_sum<L>(jy);
-    jz = group_sum<L>(jz);
-    wx = group_sum<L>(wx);
-    wy = group_sum<L>(wy);
-    wz = group_sum<L>(wz);
-    gas = group_or<L>(gas);
-    obs = group_or<L>(obs);
-    const float ux = jx / r0, uy = jy / r0, uz = jz / r0;
-    const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
-    const float rho_b = gas_density(d) + d.six_sigma * kap;
-    const bool corner = gas && obs;
-    float ntx = 0.f, nty = 0.f, ntz = 0.f;
-    if (corner) {
-        const float wl = rsqrtf(wx * wx + wy * wy + wz * wz);
-        const float vx = wx * wl, vy = wy * wl, vz = wz * wl;
-        const float wn = c4.x * vx + c4.y * vy + c4.z * vz;
-        ntx = c4.x - wn * vx;
-        nty = c4.y - wn * vy;
-        ntz = c4.z - wn * vz;
-    }
-    float g[PJ][2];
-    float dm = 0.f, rg = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-    for (int j = 0; j < PJ; ++j) {
-        const int p = r + L * j;
-        const int pp = p < 9 ? p : 0;
-        const int ex = pair_c(PAIR_CX, pp), ey = pair_c(PAIR_CY, pp), ez = pair_c(PAIR_CZ, pp);
-        const float w = pp < 3 ? 1.0f / 18.0f : 1.0f / 36.0f;
-        const float cu = ex * ux + ey * uy + ez * uz;
-        const float base2 = 2.0f * w * rho_b * (1.0f + 4.5f * cu * cu - uu);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const float sgn = h == 0 ? 1.0f : -1.0f;  // c = sgn c_p
-            const float recon = base2 - fo[j][1 - h];
-            const bool fluid = (tq[j][h] & (T_LIQ | T_IF)) != 0;
-            const float kq = (tq[j][h] & T_LIQ) ? 1.0f : 0.5f * (phix + phn[j][h]);
-            const float outdir = -sgn * (ex * ntx + ey * nty + ez * ntz);  // c_qbar . n_t
-            const float bound = ((tq[j][h] & T_OBS) && !(corner && outdir < 0.f)) ? fo[j][1 - h] : recon;
-            g[j][h] = fluid ? fin[j][h] : bound;
-            dm += (fluid && p < 9) ? kq * (fin[j][h] - fo[j][1 - h]) : 0.f;
-        }
-        if (p < 9) {
-            rg += g[j][0] + g[j][1];
-            const float dg = g[j][0] - g[j][1];
-            gx += ex * dg;
-            gy += ey * dg;
-            gz += ez * dg;
-        }
-    }
-    if (r == L - 1) rg += fo0;
-    rg = group_sum<L>(rg);
-    gx = group_sum<L>(gx);
-    gy = group_sum<L>(gy);
-    gz = group_sum<L>(gz);
-    dm = group_sum<L>(dm);
-    // collision (Eq. lbe2) of the cell's own pairs
-    const float inv = 1.0f / rg;
-    const float vx = gx * inv, vy = gy * inv, vz = gz * inv;
-    const float vv = 1.5f * (vx * vx + vy * vy + vz * vz);
-#pragma unroll
-    for (int j = 0; j < PJ; ++j) {
-        const int p = r + L * j;
-        const int pp = p < 9 ? p : 0;
-        const int ex = pair_c(PAIR_CX, pp), ey = pair_c(PAIR_CY, pp), ez = pair_c(PAIR_CZ, pp);
-        const float w = pp < 3 ? 1.0f / 18.0f : 1.0f / 36.0f;
-        const int q = 2 * pp + 1;
-        const float cu = ex * vx + ey * vy + ez * vz;
-        float a0, a1;
-        if (COLL == FSL_BGK) {
-            const float fe0 = w * rg * (1.0f + 3.0f * cu + 4.5f * cu * cu - vv);
-            const float fe1 = w * rg * (1.0f - 3.0f * cu + 4.5f * cu * cu - vv);
-            a0 = g[j][0] + d.omega_e * (fe0 - g[j][0]);
-            a1 = g[j][1] + d.omega_e * (fe1 - g[j][1]);
-        } else {
-            const float ep = w * rg * (1.0f + 4.5f * cu * cu - vv);
-            const float em = w * rg * 3.0f * cu;
-            const float fp = 0.5f * (g[j][0] + g[j][1]), fm = 0.5f * (g[j][0] - g[j][1]);
-            const float de = d.omega_e * (fp - ep), dd = d.omega_o * (fm - em);
-            a0 = g[j][0] - de - dd;
-            a1 = g[j][1] - de + dd;
-        }
-        if (act && p < 9) {
-            St::st(d.fdst, (long long)q * N + i, q, a0, d);
-            St::st(d.fdst, (long long)(q + 1) * N + i, q + 1, a1, d);
-        }
-    }
-    if (act && r == L - 1) St::st(d.fdst, i, 0, fo0 + d.omega_e * ((1.0f / 3.0f) * rg * (1.0f - vv) - fo0), d);
-    warp_append(d.slow, d.counts + C_SLOW, defer && r == 0, i);
-    if (act && r == 0) {
-        d.kappa[i] = kap;
-        const float mm = d.mass[i] + dm;
-        d.mass[i] = mm;
-        d.rho[i] = rg;
-        if (!d.frozen) {
-            if (mm > (1.0f + d.eps) * rg) {
-                d.flags[i] = fl | B_TOLIQ;
-                d.fill[atomicAdd(d.counts + C_FILL, 1)] = i;
-            } else if (mm < -d.eps * rg) {
-                d.flags[i] = fl | B_TOGAS;
-                d.empty[atomicAdd(d.counts + C_EMPTY, 1)] = i;
-            }
-        }
-    }
-}
-
-template <int S, int COLL>
-__global__ void __launch_bounds__(BRICK_THREADS, 2) k_brick(Dev d) {
+__global__ void __launch_bounds__(LIST_BLOCK, IFACE_MIN_BLOCKS) k_curv_iface_fast(Dev d) {
     pdl_enter();
-    __shared__ float4 s_nrm[BR1N];
-    __shared__ float s_phi[BR2N];
-    __shared__ uint8_t s_fl[BR2N];
-    __shared__ short s_list[BR1N];
-    __shared__ int s_n1, s_n0;
+    using St = Store<S>;
     int cnt[1];
-    block_counts<1>(d.counts, {d.cbrk}, cnt);
-    const int nb = cnt[0];
-    const int tid = threadIdx.x;
-    for (int bi = blockIdx.x; bi < nb; bi += gridDim.x) {  // block-uniform
-        const int b = d.brick_list[bi];
-        const int bx = b % d.nbx, bt = b / d.nbx, by = bt % d.nby, bz = bt / d.nby;
-        const int x0 = bx * BRK, y0 = by * BRK, z0 = bz * BRK;
-        if (tid == 0) {
-            s_n1 = 0;
-            s_n0 = 0;
+    block_counts<1>(d.counts, {d.cif}, cnt);
+    const int n = cnt[0];
+    const long long N = d.N;
+    constexpr int CPW = 32 / L;                 // cells per warp
+    constexpr int RS = (27 + L - 1) / L;        // fit rows per lane
+    constexpr int PJ = (9 + L - 1) / L;         // direction pairs per lane
+    const int lane = threadIdx.x & 31, r = lane % L;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int base = gw * CPW; base < n; base += nwarps * CPW) {  // warp-uniform
+        const int k = base + lane / L;
+        const bool valid = k < n;
+        const int i = d.iflist[valid ? k : base];
+        int x, y, z;
+        cell_coords(d, i, x, y, z);
+        // neighbour coordinates (periodic), picked by select: lane-dependent
+        // indices into small arrays would put the arrays in local memory
+        const int xm = x == 0 ? d.nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? d.ny - 1 : y - 1, yp = y == d.ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? d.nz - 1 : z - 1, zp = z == d.nz - 1 ? 0 : z + 1;
+        auto px = [&](int o) { return o < 0 ? xm : (o > 0 ? xp : x); };
+        auto py = [&](int o) { return o < 0 ? ym : (o > 0 ? yp : y); };
+        auto pz = [&](int o) { return o < 0 ? zm : (o > 0 ? zp : z); };
+        // ---- LSQR fit (FP32 normal equations), rows split over the group
+        const float4 c4 = d.normal[i];
+        uint8_t fjs[RS];
+        float4 q4s[RS];
+#pragma unroll
+        for (int s7 = 0; s7 < RS; ++s7) {
+            const int t = r + L * s7;
+            const int tt = t < 27 ? t : 13;
+            const int jj = cell_index(d, px(tt % 3 - 1), py((tt / 3) % 3 - 1), pz(tt / 9 - 1));
+            fjs[s7] = d.flags[jj];
+            q4s[s7] = d.normal[jj];
         }
-        // 1. flags and fill levels of the brick and a 2-cell halo
-        for (int k = tid; k < BR2N; k += BRICK_THREADS) {
-            const int lx = k % BR2, ly = (k / BR2) % BR2, lz = k / (BR2 * BR2);
-            const int j = cell_index(d, wrapm(x0 - 2 + lx, d.nx), wrapm(y0 - 2 + ly, d.ny), wrapm(z0 - 2 + lz, d.nz));
-            s_fl[k] = d.flags[j];
-            s_phi[k] = d.phi[j];
+        const uint8_t fl = d.flags[i];
+        const float phix = d.phi[i];
+        // ---- the stream-collide's loads (independent of kappa), issued with the fit's
+        float fo[PJ][2], fin[PJ][2], phn[PJ][2];
+        uint8_t tq[PJ][2];
+        float fo0 = 0.f;
+        float r0 = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, wx = 0.f, wy = 0.f, wz = 0.f;
+        int gas = 0, obs = 0;
+#pragma unroll
+        for (int j = 0; j < PJ; ++j) {
+            const int p = r + L * j;
+            const int pp = p < 9 ? p : 0;
+            const int ex = pair_c(PAIR_CX, pp), ey = pair_c(PAIR_CY, pp), ez = pair_c(PAIR_CZ, pp);
+            const int q = 2 * pp + 1;
+            const int sq = cell_index(d, px(-ex), py(-ey), pz(-ez));  // x - c_q
+            const int sb = cell_index(d, px(ex), py(ey), pz(ez));     // x + c_q
+            fo[j][0] = St::ld(d.fsrc, (long long)q * N + i, q, d);
+            fo[j][1] = St::ld(d.fsrc, (long long)(q + 1) * N + i, q + 1, d);
+            tq[j][0] = d.flags[sq] & T_MASK;
+            tq[j][1] = d.flags[sb] & T_MASK;
+            fin[j][0] = St::ld(d.fsrc, (long long)q * N + sq, q, d);
+            fin[j][1] = St::ld(d.fsrc, (long long)(q + 1) * N + sb, q + 1, d);
+            phn[j][0] = d.phi[sq];
+            phn[j][1] = d.phi[sb];
         }
-        __syncthreads();
-        // 2. normals and PLIC offsets of the interface cells of the brick and a 1-cell halo
-        for (int k = tid; k < BR1N; k += BRICK_THREADS) {
-            const int lx = k % BR1, ly = (k / BR1) % BR1, lz = k / (BR1 * BR1);
-            s_nrm[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (s_fl[((lz + 1) * BR2 + ly + 1) * BR2 + lx + 1] & T_IF) s_list[atomicAdd(&s_n1, 1)] = (short)k;
+        if (r == L - 1) fo0 = St::ld(d.fsrc, i, 0, d);
+        const bool nozero = !(c4.x == 0.f && c4.y == 0.f && c4.z == 0.f);
+        FastFrame F;
+        lsqr_fast_frame(nozero ? c4 : make_float4(0.f, 0.f, 1.f, 0.f), F);
+        float G[15], rv[5];
+#pragma unroll
+        for (int t = 0; t < 15; ++t) G[t] = 0.f;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) rv[t] = 0.f;
+        int m = 0;
+        bool contact = r == 0 && (fl & B_NEAR) != 0;
+#pragma unroll
+        for (int s7 = 0; s7 < RS; ++s7) {
+            const int t = r + L * s7;
+            if (t < 27) lsqr_fast_row(t, fjs[s7], q4s[s7], F, G, rv, m, contact);
         }
-        __syncthreads();
-        const int n1 = s_n1;
-        for (int e = tid; e < n1; e += BRICK_THREADS) {
-            const int k = s_list[e];
-            const int lx = k % BR1, ly = (k / BR1) % BR1, lz = k / (BR1 * BR1);
-            const int c2 = ((lz + 1) * BR2 + ly + 1) * BR2 + lx + 1;
-            float nv[3], a;
-            if (s_fl[c2] & B_NEAR) {
-                const int gx = wrapm(x0 - 1 + lx, d.nx), gy = wrapm(y0 - 1 + ly, d.ny), gz = wrapm(z0 - 1 + lz, d.nz);
-                parker_youngs<float>([&](int dx, int dy, int dz) { return phi_ext(d, gx + dx, gy + dy, gz + dz); }, nv);
+#pragma unroll
+        for (int t = 0; t < 15; ++t) G[t] = group_sum<L>(G[t]);
+#pragma unroll
+        for (int t = 0; t < 5; ++t) rv[t] = group_sum<L>(rv[t]);
+#pragma unroll
+        for (int o = 1; o < L; o <<= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+        contact = group_or<L>(contact ? 1 : 0) != 0;
+        float kap = 0.f;
+        const bool ok = nozero ? lsqr_fast_solve(G, rv, m, contact, d.fp64_cond, kap) : true;
+        if (!nozero) kap = 0.f;
+        const bool defer = valid && !ok;
+        const bool act = valid && ok;  // group-uniform
+        // ---- interface stream-collide of the cell, direction pairs over the group
+#pragma unroll
+        for (int j = 0; j < PJ; ++j) {
+            const int p = r + L * j;
+            if (p < 9) {
+                const int ex = pair_c(PAIR_CX, p), ey = pair_c(PAIR_CY, p), ez = pair_c(PAIR_CZ, p);
+                r0 += fo[j][0] + fo[j][1];
+                const float dj = fo[j][0] - fo[j][1];
+                jx += ex * dj;
+                jy += ey * dj;
+                jz += ez * dj;
+                gas |= ((tq[j][0] | tq[j][1]) & T_GAS) ? 1 : 0;
+                if (tq[j][0] & T_OBS) { obs = 1; wx -= ex; wy -= ey; wz -= ez; }
+                if (tq[j][1] & T_OBS) { obs = 1; wx += ex; wy += ey; wz += ez; }
+            }
+        }
+        if (r == L - 1) r0 += fo0;
+        r0 = group_sum<L>(r0);
+        jx = group_sum<L>(jx);
+        jy = group_sum<L>(jy);
+        jz = group_sum<L>(jz);
+        wx = group_sum<L>(wx);
+        wy = group_sum<L>(wy);
+        wz = group_sum<L>(wz);
+        gas = group_or<L>(gas);
+        obs = group_or<L>(obs);
+        const float ux = jx / r0, uy = jy / r0, uz = jz / r0;
+        const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+        const float rho_b = gas_density(d) + d.six_sigma * kap;
+        const bool corner = gas && obs;
+        float ntx = 0.f, nty = 0.f, ntz = 0.f;
+        if (corner) {
+            const float wl = rsqrtf(wx * wx + wy * wy + wz * wz);
+            const float vx = wx * wl, vy = wy * wl, vz = wz * wl;
+            const float wn = c4.x * vx + c4.y * vy + c4.z * vz;
+            ntx = c4.x - wn * vx;
+            nty = c4.y - wn * vy;
+            ntz = c4.z - wn * vz;
+        }
+        float g[PJ][2];
+        float dm = 0.f, rg = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+        for (int j = 0; j < PJ; ++j) {
+            const int p = r + L * j;
+            const int pp = p < 9 ? p : 0;
+            const int ex = pair_c(PAIR_CX, pp), ey = pair_c(PAIR_CY, pp), ez = pair_c(PAIR_CZ, pp);
+            const float w = pp < 3 ? 1.0f / 18.0f : 1.0f / 36.0f;
+            const float cu = ex * ux + ey * uy + ez * uz;
+            const float base2 = 2.0f * w * rho_b * (1.0f + 4.5f * cu * cu - uu);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float sgn = h == 0 ? 1.0f : -1.0f;  // c = sgn c_p
+                const float recon = base2 - fo[j][1 - h];
+                const bool fluid = (tq[j][h] & (T_LIQ | T_IF)) != 0;
+                const float kq = (tq[j][h] & T_LIQ) ? 1.0f : 0.5f * (phix + phn[j][h]);
+                const float outdir = -sgn * (ex * ntx + ey * nty + ez * ntz);  // c_qbar . n_t
+                const float bound = ((tq[j][h] & T_OBS) && !(corner && outdir < 0.f)) ? fo[j][1 - h] : recon;
+                g[j][h] = fluid ? fin[j][h] : bound;
+                dm += (fluid && p < 9) ? kq * (fin[j][h] - fo[j][1 - h]) : 0.f;
+            }
+            if (p < 9) {
+                rg += g[j][0] + g[j][1];
+                const float dg = g[j][0] - g[j][1];
+                gx += ex * dg;
+                gy += ey * dg;
+                gz += ez * dg;
+            }
+        }
+        if (r == L - 1) rg += fo0;
+        rg = group_sum<L>(rg);
+        gx = group_sum<L>(gx);
+        gy = group_sum<L>(gy);
+        gz = group_sum<L>(gz);
+        dm = group_sum<L>(dm);
+        // collision (Eq. lbe2) of the cell's own pairs
+        const float inv = 1.0f / rg;
+        const float vx = gx * inv, vy = gy * inv, vz = gz * inv;
+        const float vv = 1.5f * (vx * vx + vy * vy + vz * vz);
+#pragma unroll
+        for (int j = 0; j < PJ; ++j) {
+            const int p = r + L * j;
+            const int pp = p < 9 ? p : 0;
+            const int ex = pair_c(PAIR_CX, pp), ey = pair_c(PAIR_CY, pp), ez = pair_c(PAIR_CZ, pp);
+            const float w = pp < 3 ? 1.0f / 18.0f : 1.0f / 36.0f;
+            const int q = 2 * pp + 1;
+            const float cu = ex * vx + ey * vy + ez * vz;
+            float a0, a1;
+            if (COLL == FSL_BGK) {
+                const float fe0 = w * rg * (1.0f + 3.0f * cu + 4.5f * cu * cu - vv);
+                const float fe1 = w * rg * (1.0f - 3.0f * cu + 4.5f * cu * cu - vv);
+                a0 = g[j][0] + d.omega_e * (fe0 - g[j][0]);
+                a1 = g[j][1] + d.omega_e * (fe1 - g[j][1]);
             } else {
-                parker_youngs<float>([&](int dx, int dy, int dz) { return s_phi[c2 + (dz * BR2 + dy) * BR2 + dx]; },
-                                     nv);
+                const float ep = w * rg * (1.0f + 4.5f * cu * cu - vv);
+                const float em = w * rg * 3.0f * cu;
+                const float fp = 0.5f * (g[j][0] + g[j][1]), fm = 0.5f * (g[j][0] - g[j][1]);
+                const float de = d.omega_e * (fp - ep), dd = d.omega_o * (fm - em);
+                a0 = g[j][0] - de - dd;
+                a1 = g[j][1] - de + dd;
             }
-            const bool okn = unit_normal_offset<float>(nv, s_phi[c2], d.plic_iters, a);
-            const float4 n4 = okn ? make_float4(nv[0], nv[1], nv[2], a) : make_float4(0.f, 0.f, 0.f, 0.f);
-            s_nrm[k] = n4;
-            if (lx >= 1 && lx <= BRK && ly >= 1 && ly <= BRK && lz >= 1 && lz <= BRK) {
-                const int gx = x0 - 1 + lx, gy = y0 - 1 + ly, gz = z0 - 1 + lz;
-                if (gx < d.nx && gy < d.ny && gz < d.nz) d.normal[cell_index(d, gx, gy, gz)] = n4;
+            if (act && p < 9) {
+                St::st(d.fdst, (long long)q * N + i, q, a0, d);
+                St::st(d.fdst, (long long)(q + 1) * N + i, q + 1, a1, d);
             }
         }
-        __syncthreads();
-        // 3. the brick's own interface cells, BRICK_LANES lanes each
-        for (int k = tid; k < BRK * BRK * BRK; k += BRICK_THREADS) {
-            const int lx = k % BRK, ly = (k / BRK) % BRK, lz = k / (BRK * BRK);
-            if (x0 + lx >= d.nx || y0 + ly >= d.ny || z0 + lz >= d.nz) continue;
-            if (s_fl[((lz + 2) * BR2 + ly + 2) * BR2 + lx + 2] & T_IF) s_list[atomicAdd(&s_n0, 1)] = (short)k;
+        if (act && r == L - 1) St::st(d.fdst, i, 0, fo0 + d.omega_e * ((1.0f / 3.0f) * rg * (1.0f - vv) - fo0), d);
+        warp_append(d.slow, d.counts + C_SLOW, defer && r == 0, i);
+        if (act && r == 0) {
+            d.kappa[i] = kap;
+            const float mm = d.mass[i] + dm;
+            d.mass[i] = mm;
+            d.rho[i] = rg;
+            if (!d.frozen) {
+                if (mm > (1.0f + d.eps) * rg) {
+                    d.flags[i] = fl | B_TOLIQ;
+                    d.fill[atomicAdd(d.counts + C_FILL, 1)] = i;
+                } else if (mm < -d.eps * rg) {
+                    d.flags[i] = fl | B_TOGAS;
+                    d.empty[atomicAdd(d.counts + C_EMPTY, 1)] = i;
+                }
+            }
         }
-        __syncthreads();
-        const int n0 = s_n0;
-        for (int base = 0; base < n0; base += BRICK_CELLS) {  // block-uniform
-            const int e = base + tid / BRICK_LANES;
-            const bool valid = e < n0;
-            brick_cell<S, COLL, BRICK_LANES>(d, s_list[valid ? e : base], x0, y0, z0, valid, tid % BRICK_LANES, s_fl,
-                                             s_phi, s_nrm);
-        }
-        __syncthreads();  // the next brick overwrites the staged arrays
     }
 }
 
@@ -935,10 +678,10 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
 //    converted neighbours in fixed q order (and clear the mark).
 __global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
     pdl_enter();
-    int cnt[7];
-    block_counts<7>(d.counts, {d.cif, C_NEWGAS, C_LIQ2IF, C_FILL, C_EMPTY, d.cdirty, C_TAG}, cnt);
+    int cnt[6];
+    block_counts<6>(d.counts, {d.cif, C_NEWGAS, C_LIQ2IF, C_FILL, C_EMPTY, d.cdirty}, cnt);
     if (blockIdx.x == 0 && threadIdx.x == 0 && cnt[5]) d.counts[C_SEG] = 0;  // filled again by k_fin_b
-    const int nold = cnt[0], ngas = cnt[1], nliq = cnt[2], tag = cnt[6];
+    const int nold = cnt[0], ngas = cnt[1], nliq = cnt[2];
     const bool any = (cnt[3] + cnt[4]) > 0;
     long long phisum = 0;  // bubble model: fixed-point fill levels of the next interface cells
     warp_uniform_loop(nold + ngas + nliq, [&](int k, bool valid) {
@@ -969,12 +712,6 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
                 d.phi[i] = ph;
                 if (d.bub_i) phisum += __double2ll_rn((double)ph * BUB_FIX);
                 keep = true;
-                // the cell's brick joins the brick list of t+1 (once: the tag of this step)
-                int x, y, z;
-                cell_coords(d, i, x, y, z);
-                const int b = brick_of(d, x, y, z);
-                if (__ldcg(d.brick_tag + b) != tag && atomicExch(d.brick_tag + b, tag) != tag)
-                    d.brick_list_next[atomicAdd(d.counts + d.cbrk_next, 1)] = b;
             }
         }
         warp_append(d.iflist_next, d.counts + d.cif_next, keep, i);
@@ -1061,39 +798,10 @@ void launch_seg_compact(const Dev &d, cudaStream_t s) {
     k_seg_compact<<<(d.nseg + 255) / 256, 256, 0, s>>>(d);
 }
 
-// bricks of the current interface list -> brick list (tags with the current
-// step tag; the caller resets the tags and the list counter)
-__global__ void __launch_bounds__(256) k_brick_build(Dev d) {
-    int cnt[2];
-    block_counts<2>(d.counts, {d.cif, C_TAG}, cnt);
-    const int n = cnt[0], tag = cnt[1];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        int x, y, z;
-        cell_coords(d, d.iflist[k], x, y, z);
-        const int b = brick_of(d, x, y, z);
-        if (atomicExch(d.brick_tag + b, tag) != tag) d.brick_list[atomicAdd(d.counts + d.cbrk, 1)] = b;
-    }
-}
 
-void launch_brick_build(const Dev &d, cudaStream_t s) {
-    static const int g = list_blocks((const void *)k_brick_build, 256, 2);
-    k_brick_build<<<g, 256, 0, s>>>(d);
-}
-
-__global__ void k_step_begin(Dev d) {
-    pdl_enter();
-    if (threadIdx.x == 0) step_prologue(d);
-}
-
-void launch_step_begin(const Dev &d, cudaStream_t s) { k_step_begin<<<1, 32, 0, s>>>(d); }
 
 template <int S, int COLL>
 void launch_bulk(const Dev &d, cudaStream_t s) {
-    if (S != FSL_F32 && d.nx % 8 == 0) {  // 16-byte aligned rows: bulk-staged source rows
-        static const int g16 = resident_grid((const void *)k_sc_bulk16<S == FSL_F32 ? FSL_F16_OFS : S, COLL>, 256);
-        k_sc_bulk16<S == FSL_F32 ? FSL_F16_OFS : S, COLL><<<g16, 256, 0, s>>>(d);
-        return;
-    }
     static const int gb = resident_grid((const void *)k_sc_bulk<S, COLL>, 256);
     k_sc_bulk<S, COLL><<<gb, 256, 0, s>>>(d);
 }
@@ -1116,9 +824,9 @@ void launch_iface(const Dev &d, cudaStream_t s) {
 
 template <int S, int COLL>
 void launch_ci(const Dev &d, cudaStream_t s) {
-    static const int gb = resident_grid((const void *)k_brick<S, COLL>, BRICK_THREADS);
+    static const int gf = list_blocks((const void *)k_curv_iface_fast<S, COLL, FSL_IFACE_LANES>, LIST_BLOCK, 4);
     static const int gs = list_blocks((const void *)k_curv_iface_slow<S, COLL>, LIST_BLOCK, 1);
-    launch_pdl(k_brick<S, COLL>, gb, BRICK_THREADS, s, d);
+    launch_pdl(k_curv_iface_fast<S, COLL, FSL_IFACE_LANES>, gf, LIST_BLOCK, s, d);
     launch_pdl(k_curv_iface_slow<S, COLL>, gs, LIST_BLOCK, s, d);
 }
 

@@ -15,9 +15,11 @@ def test_algorithmic_bytes_per_cell():
     nb16 = bench.algorithmic_bytes(n_fluid=1000, n_if=100, n_seg_cells=1000, pdf_bytes=2)
     assert nb16["sc_liquid"] == 76.0 * 900 + 1000
     assert nb16["sc_interface"] == 134.0 * 100
+    # the LSQR fit fused with the interface stream-collide
     fused = bench.algorithmic_bytes(n_fluid=1000, n_if=100, n_seg_cells=1000, fused=True)
     assert fused["sc_interface"] == 0.0
     assert fused["lsqr_curvature"] == nb["lsqr_curvature"] + nb["sc_interface"]
+    assert fused["lsqr_curvature"] == (21.0 + 248.0) * 100
 
 
 def test_roofline_fraction_is_bytes_over_time_over_peak():
