@@ -456,7 +456,8 @@ def learned_curvature(F, S, stream, flush, peaks, seed, n_train, epochs, steps, 
     out["training"] = {"stencils": n_train, "sub_samples": 8, "noise": 1e-3, "stencils_per_s": n_train / gen_s,
                        "epochs": epochs, "batch": B, "steps": nsteps, "samples_per_s": nsteps * B / train_s,
                        "final_batch_loss": float(losses[-1].item()),
-                       "loop": "fsl_mlp_train_epoch (device gather + step kernels, one C-ABI call per epoch)",
+                       "last_epoch_mean_loss": float(losses.double().mean().item()),
+                       "loop": "fsl_mlp_train_epoch: per batch one fused tensor-core tile kernel (rows gathered by the permutation) and one reduction + Adam kernel, one C-ABI call per epoch",
                        "flops_per_sample": 3 * 2 * (128 * 128 * 2 + 128)}
     del X, target
     torch.cuda.empty_cache()
@@ -1133,8 +1134,9 @@ def main():
         from paper_1509_07691_gb300 import fsl as F
         lc = learned_curvature(F, S, torch.cuda.current_stream(), None, {}, S.SEED, args.mlp_train, args.mlp_epochs, 0,
                                inference=False, batch=args.mlp_batch)
-        lc.pop("heldout")
+        held = lc.pop("heldout")
         lc.pop("net")
+        lc["heldout_kappa_rel_err"] = heldout_errors(held)
         print(json.dumps({"learned_curvature": lc}))
         return
     if args.physics:

@@ -50,7 +50,7 @@ enum : uint8_t {
 // two "segment set changed" flags (one per step parity: a step sets its own,
 // clears the next step's, and rebuilds the segment list only if it is set)
 enum { C_IF0 = 0, C_IF1 = 1, C_FILL = 2, C_EMPTY = 3, C_NEWGAS = 4, C_LIQ2IF = 5, C_FP64 = 6, C_SEG = 7, C_SLOW = 8,
-       C_MLP = 9, C_MLPKEEP = 10, C_ADJ64 = 11, C_SEGD0 = 12, C_SEGD1 = 13, C_NCOUNT = 16 };
+       C_MLP = 9, C_MLPKEEP = 10, C_ADJ64 = 11, C_SEGD0 = 12, C_SEGD1 = 13, C_ADJGEN = 14, C_NCOUNT = 16 };
 
 // the grid is walked in x-row segments of SEG cells (one warp each); a
 // segment is active while it holds a liquid or interface cell
@@ -327,13 +327,12 @@ void launch_mlp_curv(const Dev &d, float *kappa_out, cudaStream_t s);
 int launch_mlp_forward_tc(const uint8_t *params, const __nv_bfloat16 *X, int n, float *y, float *z1, float *z2,
                           cudaStream_t s);
 int mlp_tc_status(bool reset);
-// weight gradients of the MLP on the tcgen05 tensor cores (k_mlp_tc.cu);
-// partial holds mlp_wgrad_partial_floats(n) floats
-size_t mlp_wgrad_partial_floats(int n);
-int launch_mlp_delta_tc(const uint8_t *params, const float *y, const float *target, int n, const float *z1,
-                        const float *z2, float *d1, float *d2, float *d3, cudaStream_t s);
-int launch_mlp_wgrad_tc(const __nv_bfloat16 *X, const float *z1, const float *d1, const float *d2, int n, float *partial,
-                        float *gW1, float *gW2, cudaStream_t s);
+// one training step's forward, deltas and gradient partials on the tensor cores,
+// one CTA per 128 rows of the batch (rows perm[row0 ..] of X, or row0 .. when
+// perm is null); part holds mlp_tile_partial_floats(n) floats, lpart one double per tile
+size_t mlp_tile_partial_floats(int n);
+int launch_mlp_train_tile(const uint8_t *params, const __nv_bfloat16 *X, const float *target, const int64_t *perm,
+                          long long row0, int n, long long n_all, float *part, double *lpart, cudaStream_t s);
 void launch_fin_frozen(const Dev &d, cudaStream_t s);
 // bubble model: liquid cells, non-obstacle cells and the fixed-point fill-level
 // sum of the current state into d.bub_i (entries of the current parity and [4])

@@ -147,118 +147,44 @@ __device__ void warp_mlp(const MlpSmem &s, const __nv_bfloat16 *Xw, float &y_lo,
 
 
 
-// ---- backward (FP32): deltas, then weight gradients ------------------------
-// loss = (1/n) sum w (y - t)^2, w = 1/(t^2 + 7e-5)
-// bias gradients and dw3 = sum_n d3 h2, db3 = sum_n d3: partial sums over
-// chunks of VG_ROWS samples, then a fixed-order sum over the chunks.  A chunk
-// is one block of VG_GROUPS x 128 threads: group g sums rows [16 g, 16 g + 16)
-// of the chunk with all sixteen rows' loads in flight (a rolled loop waited
-// out one DRAM round trip per row), and group 0 adds the groups in order.
-constexpr int VG_GROUPS = 4;
-constexpr int VG_SUB = 16;
-constexpr int VG_ROWS = VG_GROUPS * VG_SUB;
+// ---- training: gradient reduction and Adam --------------------------------------
+// (forward, deltas and the per-tile gradient partials run on the tensor cores
+// in k_mlp_train_tile, k_mlp_tc.cu)
+// Sum of the per-tile partials of k_mlp_train_tile in tile order into the
+// gradient (master layout), and, with master != null, the Adam step on it in
+// the same thread (as k_mlp_adam).  Thread 0 also sums the tiles' loss terms.
+constexpr int PART_STRIDE = 2 * MK * MK + 4 * MK;  // floats of one tile's partials
 
-__global__ void __launch_bounds__(VG_GROUPS * MK) k_mlp_vgrad_part(const float *z2, const float *d1,
-                                                                   const float *d2, const float *d3, int n,
-                                                                   float *vpart) {
-    __shared__ float red[VG_GROUPS - 1][4][MK];
-    const int i = threadIdx.x % MK, g = threadIdx.x / MK;
-    const long long r0 = (long long)blockIdx.x * VG_ROWS + g * VG_SUB;
-    const int m = (int)max(0LL, min((long long)VG_SUB, (long long)n - r0));
-    float a1[VG_SUB], a2[VG_SUB], az[VG_SUB], a3[VG_SUB];
-#pragma unroll
-    for (int u = 0; u < VG_SUB; ++u) {
-        const bool ok = u < m;
-        const long long r = r0 + u;
-        a1[u] = ok ? d1[r * MK + i] : 0.f;
-        a2[u] = ok ? d2[r * MK + i] : 0.f;
-        az[u] = ok ? z2[r * MK + i] : 0.f;
-        a3[u] = ok ? d3[r] : 0.f;
+__global__ void __launch_bounds__(256) k_mlp_tile_reduce(const float *part, const double *lpart, int ntiles, int n,
+                                                         float *grad, float *loss,
+                                                         uint8_t *params, float *master, float *m, float *v, float lr,
+                                                         float bc1, float bc2) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e == 0 && loss) {
+        double l = 0.0;
+        for (int t = 0; t < ntiles; ++t) l += lpart[t];
+        loss[0] = (float)(l / n);
     }
-    float s[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int u = 0; u < VG_SUB; ++u) {
-        s[0] += a1[u];
-        s[1] += a2[u];
-        s[2] += a3[u] * gelu(az[u]);
-        s[3] += a3[u];
-    }
-    if (g > 0)
-        for (int k = 0; k < 4; ++k) red[g - 1][k][i] = s[k];
-    __syncthreads();
-    if (g > 0) return;
-    for (int h = 0; h < VG_GROUPS - 1; ++h)
-        for (int k = 0; k < 4; ++k) s[k] += red[h][k][i];
-    float *v = vpart + (size_t)blockIdx.x * 4 * MK;
-    v[i] = s[0];
-    v[MK + i] = s[1];
-    v[2 * MK + i] = s[2];
-    v[3 * MK + i] = i == 0 ? s[3] : 0.f;
-}
-
-// one block per gradient vector (db1, db2, dw3, db3), thread per output; the
-// chunk partials are summed in order, sixteen loads in flight per thread
-__global__ void __launch_bounds__(MK) k_mlp_vgrad_sum(const float *vpart, int nb, float *grad) {
-    const int i = threadIdx.x, vec = blockIdx.x;
-    const float *v = vpart + vec * MK + i;
+    if (e >= M_COUNT) return;
     float acc = 0.f;
-    int b = 0;
-    for (; b + 16 <= nb; b += 16) {
-        float t[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) t[u] = v[(size_t)(b + u) * 4 * MK];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) acc += t[u];
+    if (e < M_W3) {
+        const int mat = e / (MK * MK), k = e % (MK * MK);
+        const float *P = part + (size_t)mat * MK * MK + k;
+        for (int t = 0; t < ntiles; ++t) acc += P[(size_t)t * PART_STRIDE];
+    } else {
+        int vec, c = 0;
+        if (e < M_B1) { vec = 2; c = e - M_W3; }
+        else if (e < M_B2) { vec = 0; c = e - M_B1; }
+        else if (e < M_B3) { vec = 1; c = e - M_B2; }
+        else { vec = 3; }
+        const float *P = part + (size_t)2 * MK * MK + (size_t)vec * MK + c;
+        for (int t = 0; t < ntiles; ++t) acc += P[(size_t)t * PART_STRIDE];
     }
-    for (; b < nb; ++b) acc += v[(size_t)b * 4 * MK];
-    if (vec == 0) grad[M_B1 + i] = acc;
-    else if (vec == 1) grad[M_B2 + i] = acc;
-    else if (vec == 2) grad[M_W3 + i] = acc;
-    else if (i == 0) grad[M_B3] = acc;
-}
-
-// loss (1/n) sum w (y - t)^2, fixed-order reduction in one block
-// Each term in FP32 (the FP64 divide rate of one SM made this kernel the
-// slowest of a training step), summed in FP64 in a fixed order.
-__global__ void __launch_bounds__(1024) k_mlp_loss(const float *y, const float *target, int n, float *loss) {
-    __shared__ double red[1024];
-    double s = 0.0;
-    for (long long r = threadIdx.x; r < n; r += blockDim.x) {
-        const float tt = target[r], e = y[r] - tt;
-        s += (double)(e * e / (tt * tt + 7e-5f));
-    }
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 512; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) loss[0] = (float)(red[0] / n);
-}
-
-// Batch rows perm[0 .. rows) of X ([n][128] BF16) and target into Xb, tb: one
-// thread per 16-byte piece of a row.  An index outside [0, n) gathers a zero
-// row and target 0.
-constexpr int ROW_PIECES = MK * 2 / 16;
-__global__ void __launch_bounds__(256) k_mlp_gather(const uint4 *X, const float *target, const int64_t *perm, int rows,
-                                                    int n, uint4 *Xb, float *tb) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)rows * ROW_PIECES) return;
-    const int r = (int)(t / ROW_PIECES), c = (int)(t % ROW_PIECES);
-    const long long src = perm[r];
-    const bool ok = src >= 0 && src < n;
-    Xb[(long long)r * ROW_PIECES + c] = ok ? X[src * ROW_PIECES + c] : make_uint4(0u, 0u, 0u, 0u);
-    if (c == 0) tb[r] = ok ? target[src] : 0.f;
-}
-
-// Adam on the FP32 master parameters; refreshes the packed BF16 weights and FP32 biases
-__global__ void __launch_bounds__(256) k_mlp_adam(uint8_t *params, float *master, float *m, float *v,
-                                                  const float *grad, float lr, float bc1, float bc2) {
-    __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(params);
-    float *bias = reinterpret_cast<float *>(params + MB_BIAS);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M_COUNT; e += gridDim.x * blockDim.x) {
-        const float g = grad[e];
-        const float mm = 0.9f * m[e] + 0.1f * g, vv = 0.999f * v[e] + 0.001f * g * g;
+    if (grad) grad[e] = acc;
+    if (master) {
+        __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(params);
+        float *bias = reinterpret_cast<float *>(params + MB_BIAS);
+        const float mm = 0.9f * m[e] + 0.1f * acc, vv = 0.999f * v[e] + 0.001f * acc * acc;
         m[e] = mm;
         v[e] = vv;
         const float w = master[e] - lr * (mm / bc1) / (sqrtf(vv / bc2) + 1e-8f);
@@ -449,20 +375,29 @@ __global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp_curv(Dev d, float *kappa
     int evaluated = 0, kept = 0;
     for (int base = blockIdx.x * MLP_ROWS + warp * 16; base < n; base += gridDim.x * MLP_ROWS) {
         const int nvalid = n - base < 16 ? n - base : 16;
+        // the 16 cells' coordinates (lane r holds cell r), then their 5x5x5
+        // gathers four cells at a time, so that 32 loads per lane are in flight
+        int cx0 = 0, cy0 = 0, cz0 = 0;
+        if (lane < nvalid) cell_coords(d, d.iflist[base + lane], cx0, cy0, cz0);
+        unsigned obsm = 0u;  // bit r: an obstacle cell in row r's stencil (this lane's elements)
+#pragma unroll 4
         for (int r = 0; r < 16; ++r) {
-            bool obs = false;
+            const int x = __shfl_sync(0xffffffffu, cx0, r), y = __shfl_sync(0xffffffffu, cy0, r),
+                      z = __shfl_sync(0xffffffffu, cz0, r);
             if (r < nvalid) {
-                int x, y, z;
-                cell_coords(d, d.iflist[base + r], x, y, z);
-                for (int e = lane; e < 125; e += 32) {
-                    const int j = nbr_index(d, x, y, z, e / 25 - 2, (e / 5) % 5 - 2, e % 5 - 2);
-                    rw[r * MK + e] = d.phi[j];
-                    obs |= (d.flags[j] & T_OBS) != 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int e = lane + 32 * t;
+                    if (e < 125) {
+                        const int j = nbr_index(d, x, y, z, e / 25 - 2, (e / 5) % 5 - 2, e % 5 - 2);
+                        rw[r * MK + e] = d.phi[j];
+                        obsm |= (d.flags[j] & T_OBS) ? (1u << r) : 0u;
+                    }
                 }
             }
-            obs = __any_sync(0xffffffffu, obs);
-            if (lane == 0) wall[warp * 16 + r] = obs;
         }
+        obsm = __reduce_or_sync(0xffffffffu, obsm);
+        if (lane < 16) wall[warp * 16 + lane] = (obsm >> lane) & 1u;
         __syncwarp();
         if (lane < 16) cw[warp * 16 + lane] = canon_of(rw + lane * MK);
         __syncwarp();
@@ -525,32 +460,25 @@ extern "C" {
 size_t fsl_mlp_param_bytes(void) { return MB_BIAS + (size_t)(2 * MK + 1) * sizeof(float); }
 int fsl_mlp_master_count(void) { return M_COUNT; }
 
-// training workspace, in floats: z1, z2, d1, d2 ([n][128] each, first so that
-// their rows stay 16-byte aligned), y, d3, grad, the weight-gradient partials
-// of the tensor-core kernel and the bias-gradient partials, each 64-aligned
+// training workspace (bytes, each part 256-aligned): the gradient (master
+// layout), the per-tile partials of the tile kernel and the tiles' loss sums
+static size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 struct TrainWs {
-    size_t z1, z2, d1, d2, y, d3, grad, wpart, vpart, total;
+    size_t grad, part, lpart, total;
 };
-static size_t up64(size_t v) { return (v + 63) / 64 * 64; }
 static TrainWs train_ws(int n) {
     TrainWs w;
     size_t o = 0;
-    w.z1 = o; o += (size_t)n * MK;
-    w.z2 = o; o += (size_t)n * MK;
-    w.d1 = o; o += (size_t)n * MK;
-    w.d2 = o; o += (size_t)n * MK;
-    w.y = o; o = up64(o + n);
-    w.d3 = o; o = up64(o + n);
-    w.grad = o; o = up64(o + M_COUNT);
-    w.wpart = o; o = up64(o + mlp_wgrad_partial_floats(n));
-    w.vpart = o; o = up64(o + (size_t)((n + VG_ROWS - 1) / VG_ROWS) * 4 * MK);
+    w.grad = o; o = up256(o + (size_t)M_COUNT * sizeof(float));
+    w.part = o; o = up256(o + mlp_tile_partial_floats(n) * sizeof(float));
+    w.lpart = o; o = up256(o + (size_t)((n + MK - 1) / MK) * sizeof(double));
     w.total = o;
     return w;
 }
 
 size_t fsl_mlp_train_workspace(int n) {
     if (n <= 0) return 0;
-    return train_ws(n).total * sizeof(float) + 1024;
+    return train_ws(n).total + 1024;
 }
 
 int fsl_mlp_stencils(int n, const float *axes, const float *quat, const float *dir, const float *delta,
@@ -574,65 +502,47 @@ int fsl_mlp_forward(const void *params, const void *X, int n, float *y, float *z
 
 int fsl_mlp_status(int reset) { return mlp_tc_status(reset != 0); }
 
-// forward + loss + backward into grad (master layout); workspace from fsl_mlp_train_workspace(n)
-static int mlp_grad(const void *params, const void *X, const float *target, int n, float *loss_dev, void *workspace,
-                    float **grad_out, cudaStream_t s) {
-    float *ws = static_cast<float *>(workspace);
+// One training step's gradient (and with master non-null the Adam step): the
+// tile kernel over the batch rows perm[row0 .. row0 + n) of X (rows row0 ..
+// when perm is null), then the fixed-order reduction of its partials.
+static int mlp_step(const void *params, const void *X, const float *target, const int64_t *perm, long long row0, int n,
+                    long long n_all, float *loss_dev, void *workspace, float *grad_out, void *params_rw, float *master,
+                    float *m, float *v, float lr, int step, cudaStream_t s) {
+    char *ws = static_cast<char *>(workspace);
     const TrainWs L = train_ws(n);
-    float *z1 = ws + L.z1, *z2 = ws + L.z2, *d1 = ws + L.d1, *d2 = ws + L.d2, *y = ws + L.y, *d3 = ws + L.d3;
-    float *grad = ws + L.grad;
-    int rc = fsl_mlp_forward(params, X, n, y, z1, z2, s);
+    float *part = reinterpret_cast<float *>(ws + L.part);
+    double *lpart = reinterpret_cast<double *>(ws + L.lpart);
+    const int rc = launch_mlp_train_tile(static_cast<const uint8_t *>(params), static_cast<const __nv_bfloat16 *>(X),
+                                         target, perm, row0, n, n_all, part, lpart, s);
     if (rc != FSL_OK) return rc;
-    if (loss_dev) k_mlp_loss<<<1, 1024, 0, s>>>(y, target, n, loss_dev);
-    rc = launch_mlp_delta_tc(static_cast<const uint8_t *>(params), y, target, n, z1, z2, d1, d2, d3, s);
-    if (rc != FSL_OK) return rc;
-    rc = launch_mlp_wgrad_tc(static_cast<const __nv_bfloat16 *>(X), z1, d1, d2, n, ws + L.wpart, grad + M_W1,
-                             grad + M_W2, s);
-    if (rc != FSL_OK) return rc;
-    const int nb = (n + VG_ROWS - 1) / VG_ROWS;
-    k_mlp_vgrad_part<<<nb, VG_GROUPS * MK, 0, s>>>(z2, d1, d2, d3, n, ws + L.vpart);
-    k_mlp_vgrad_sum<<<4, MK, 0, s>>>(ws + L.vpart, nb, grad);
-    *grad_out = grad;
+    const float bc1 = master ? (float)(1.0 - pow(0.9, step)) : 1.f, bc2 = master ? (float)(1.0 - pow(0.999, step)) : 1.f;
+    k_mlp_tile_reduce<<<(M_COUNT + 255) / 256, 256, 0, s>>>(part, lpart, (n + MK - 1) / MK, n, grad_out, loss_dev,
+                                                           static_cast<uint8_t *>(params_rw), master, m, v, lr, bc1, bc2);
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
 }
 
 int fsl_mlp_gradients(const void *params, const void *X, const float *target, int n, float *grad, float *loss_dev,
                       void *workspace, void *stream) {
     if (!params || !X || !target || !grad || !workspace || n <= 0) return FSL_EINVAL;
-    float *g = nullptr;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int rc = mlp_grad(params, X, target, n, loss_dev, workspace, &g, s);
-    if (rc != FSL_OK) return rc;
-    return cudaMemcpyAsync(grad, g, M_COUNT * sizeof(float), cudaMemcpyDeviceToDevice, s) == cudaSuccess ? FSL_OK
-                                                                                                       : FSL_ECUDA;
-}
-
-// gradients, then Adam with bias correction for step `step` (counted from 1)
-static int train_step(void *params, float *master, float *m, float *v, const void *X, const float *target, int n,
-                      float lr, int step, float *loss_dev, void *workspace, cudaStream_t s) {
-    float *g = nullptr;
-    const int rc = mlp_grad(params, X, target, n, loss_dev, workspace, &g, s);
-    if (rc != FSL_OK) return rc;
-    const float bc1 = (float)(1.0 - pow(0.9, step)), bc2 = (float)(1.0 - pow(0.999, step));
-    k_mlp_adam<<<(M_COUNT + 255) / 256, 256, 0, s>>>(static_cast<uint8_t *>(params), master, m, v, g, lr, bc1, bc2);
-    return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
+    if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(workspace) % 256) return FSL_EINVAL;
+    return mlp_step(params, X, target, nullptr, 0, n, n, loss_dev, workspace, grad, nullptr, nullptr, nullptr, nullptr,
+                    0.f, 1, (cudaStream_t)stream);
 }
 
 int fsl_mlp_train_step(void *params, float *master, float *m, float *v, const void *X, const float *target, int n,
                        float lr, int step, float *loss_dev, void *workspace, void *stream) {
     if (!params || !master || !m || !v || !X || !target || !workspace || n <= 0 || step < 1 || !(lr > 0.f))
         return FSL_EINVAL;
-    return train_step(params, master, m, v, X, target, n, lr, step, loss_dev, workspace, (cudaStream_t)stream);
+    if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(workspace) % 256) return FSL_EINVAL;
+    return mlp_step(params, X, target, nullptr, 0, n, n, loss_dev, workspace, nullptr, params, master, m, v, lr, step,
+                    (cudaStream_t)stream);
 }
 
-// epoch workspace: the gathered batch rows (BF16) and targets, then the training workspace
-static size_t up256(size_t v) { return (v + 255) / 256 * 256; }
-static size_t epoch_rows_bytes(int batch) { return up256((size_t)batch * MK * sizeof(__nv_bfloat16)); }
-static size_t epoch_target_bytes(int batch) { return up256((size_t)batch * sizeof(float)); }
-
+// the epoch loop reads its batches through the permutation inside the tile
+// kernel: the epoch workspace is the training workspace of one batch
 size_t fsl_mlp_epoch_workspace(int batch) {
     if (batch <= 0) return 0;
-    return epoch_rows_bytes(batch) + epoch_target_bytes(batch) + fsl_mlp_train_workspace(batch);
+    return fsl_mlp_train_workspace(batch);
 }
 
 int fsl_mlp_train_epoch(void *params, float *master, float *m, float *v, const void *X, const float *target,
@@ -643,17 +553,11 @@ int fsl_mlp_train_epoch(void *params, float *master, float *m, float *v, const v
         return FSL_EINVAL;
     if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(workspace) % 256) return FSL_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    char *ws = static_cast<char *>(workspace);
-    uint4 *Xb = reinterpret_cast<uint4 *>(ws);
-    float *tb = reinterpret_cast<float *>(ws + epoch_rows_bytes(batch));
-    void *tws = ws + epoch_rows_bytes(batch) + epoch_target_bytes(batch);
     const int nb = n / batch;
-    const int gblocks = (int)(((long long)batch * ROW_PIECES + 255) / 256);
     for (int b = 0; b < nb; ++b) {
-        k_mlp_gather<<<gblocks, 256, 0, s>>>(static_cast<const uint4 *>(X), target, perm + (long long)b * batch, batch,
-                                             n, Xb, tb);
-        const int rc = train_step(params, master, m, v, Xb, tb, batch, lr, step0 + b + 1,
-                                  losses_dev ? losses_dev + b : nullptr, tws, s);
+        const int rc = mlp_step(params, X, target, perm, (long long)b * batch, batch, n,
+                                losses_dev ? losses_dev + b : nullptr, workspace, nullptr, params, master, m, v, lr,
+                                step0 + b + 1, s);
         if (rc != FSL_OK) return rc;
     }
     return FSL_OK;

@@ -251,173 +251,130 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_forward_tc(const uint8_t 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-// ---- weight gradients on the tensor cores -------------------------------------
-// dW1[o][i] = sum_b d1[b][o] x[b][i] and dW2[o][i] = sum_b d2[b][o] h1[b][i]
-// (h1 = bf16(gelu(z1)), as the forward feeds layer 2): one CTA per 128-sample
-// chunk of the batch and matrix, an MMA group with M = o, N = i, K = b over
-// the chunk (both operands staged transposed into the K-major tile, in BF16),
-// the 128 x 128 partial written to partial[mat][chunk]; k_mlp_wreduce sums
-// the chunks in a fixed order.
-struct WgSmem {
-    __nv_bfloat16 A[TILE * TILE];
-    __nv_bfloat16 B[TILE * TILE];
-    uint32_t tmem_base;
-    unsigned long long mbar;
-};
-
-__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_wgrad_tc(const __nv_bfloat16 *X, const float *z1, const float *d1,
-                                                               const float *d2, int n, float *partial, int *status) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    WgSmem &s = *reinterpret_cast<WgSmem *>(smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mat = blockIdx.y, chunk = blockIdx.x, nchunk = gridDim.x;
-    const long long b0 = (long long)chunk * TILE;
-    const int rows = (int)min((long long)TILE, n - b0);
-    const float *D = mat == 0 ? d1 : d2;
-    char *At = reinterpret_cast<char *>(s.A), *Bt = reinterpret_cast<char *>(s.B);
-    // A[o][b] = D[b0 + b][o], B[i][b] = x or h1 at [b0 + b][i]: thread per (b, 8 columns)
-    for (int c = threadIdx.x; c < TILE * TILE / 8; c += blockDim.x) {
-        const int b = c >> 4, c8 = (c & 15) * 8;
-        float av[8], bv[8];
-        if (b < rows) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(D + (b0 + b) * TILE + c8);
-            const float4 a1 = *reinterpret_cast<const float4 *>(D + (b0 + b) * TILE + c8 + 4);
-            av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w; av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
-            if (mat == 0) {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) bv[e] = __bfloat162float(X[(b0 + b) * TILE + c8 + e]);
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) bv[e] = gelu_tc(z1[(b0 + b) * TILE + c8 + e]);
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) av[e] = bv[e] = 0.f;
-        }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            *reinterpret_cast<__nv_bfloat16 *>(At + tile_off(c8 + e, b)) = __float2bfloat16_rn(av[e]);
-            *reinterpret_cast<__nv_bfloat16 *>(Bt + tile_off(c8 + e, b)) = __float2bfloat16_rn(bv[e]);
-        }
-    }
-    if (threadIdx.x == 0) {
-        mbar_init(&s.mbar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem_base)),
-                     "r"(TILE)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    proxy_fence();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = s.tmem_base;
-    if (threadIdx.x == 0) {
-        const uint32_t aA = smem_u32(s.A), aB = smem_u32(s.B);
-#pragma unroll
-        for (int kk = 0; kk < TILE / 16; ++kk)
-            tc_mma(tmem, smem_desc(aA + kk * 2 * CORE_K, CORE_K, CORE_MN), smem_desc(aB + kk * 2 * CORE_K, CORE_K, CORE_MN),
-                   kk > 0);
-        tc_commit(&s.mbar);
-    }
-    const bool ok = !__syncthreads_or(mbar_wait(&s.mbar, 0) ? 0 : 1);
-    if (ok) {
-        tc_fence_after();
-        const int o = 32 * (warp & 3) + lane, col0 = 64 * (warp >> 2);
-        float *P = partial + ((size_t)mat * nchunk + chunk) * TILE * TILE + (size_t)o * TILE;
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-            const int c = col0 + 16 * cc;
-            float v[16];
-            tc_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c, v);
-#pragma unroll
-            for (int e = 0; e < 16; e += 4) *reinterpret_cast<float4 *>(P + c + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
-        }
-    } else if (threadIdx.x == 0) {
-        set_status(status, FSL_ETIMEOUT);
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TILE) : "memory");
-}
-
-// ---- deltas on the tensor cores ------------------------------------------------
-// d3 = dL/dy = 2 (y - t) / ((t^2 + 7e-5) n), d2 = d3 w3 gelu'(z2) (FP32, as
-// stored for the weight and bias gradients), d1 = (d2 W2) gelu'(z1) with the
-// product d2 W2 as an MMA: M = sample b, N = i, K = o, d2 rounded to BF16,
-// W2 staged transposed (B[i][o] = W2[o][i]).  One CTA per 128-sample chunk.
+// derivative of the GELU (erf form)
 __device__ __forceinline__ float gelu_grad_tc(float x) {
     return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
-struct DtSmem {
-    __nv_bfloat16 A[TILE * TILE];
-    __nv_bfloat16 B[TILE * TILE];
-    float w3[TILE];
-    float d3[TILE];
+// ---- one training step on the tensor cores, one CTA per 128-row tile --------------
+// Forward, loss, deltas and the weight-gradient partials of a tile in one
+// kernel: five 128 x 128 x 128 MMA groups on operands kept in shared memory,
+// accumulators in TMEM, and the elementwise work in the epilogues between
+// them.  Five operand tiles (T0..T4, 32 KB each) change roles as the step
+// goes on:
+//   load   T0 = X[b][i], T4 = X^T[i][b] (rows gathered through perm),
+//          T1 = W1[o][i], T2 = W2[o][h], T3 = W2^T[h][o]
+//   L1     D[0..127]   = T0 T1^T            z1 = D + b1
+//   E1     T0 = h1[b][h] = bf16(gelu(z1)),  T1 = h1^T[h][b]
+//   L2     D[128..255] = T0 T2^T            z2 = D + b2, y = gelu(z2) . w3 + b3
+//   E2     d3 = 2 (y - t) / ((t^2 + 7e-5) n), d2 = d3 w3 gelu'(z2) (FP32);
+//          T0 = bf16(d2)[b][o], T2 = bf16(d2)^T[o][b]
+//   delta  D[256..383] = T0 T3^T  (= d2 W2)  d1 = D gelu'(z1) (FP32), T3 = bf16(d1)^T[o][b]
+//   wgrad  D[384..511] = T3 T4^T  (= d1^T X, dW1),  D[128..255] = T2 T1^T  (= d2^T h1, dW2)
+//   E4     the tile's partials to part[tile] (PART_STRIDE floats: dW1, dW2,
+//          then the column sums of d1, d2, d3 gelu(z2) and d3, that is db1,
+//          db2, dw3, db3 at [0]); the tile's loss terms (FP32 terms, FP64 sum
+//          in row order) to lpart[tile].
+// The operand layouts are those of the forward, delta and weight-gradient
+// kernels above (K-major tiles, transposes written element by element).  Column
+// sums reduce over the 32 rows of a warp by a fixed shuffle tree and over the
+// four row quarters in order.  Rows past the batch end are zero (their deltas
+// are 0).  Every MMA wait is bounded; a timeout records FSL_ETIMEOUT, skips the
+// rest and still frees the tensor memory.
+constexpr int PART_STRIDE = 2 * TILE * TILE + 4 * TILE;
+constexpr int FT_THREADS = 512;  // 16 warps: four per TMEM lane quarter, 32 columns each
+
+// Sum over the 32 lanes of a warp of 16 values per lane, scattered: lane l
+// returns the total of value l % 16.  A fixed butterfly: each stage a lane
+// keeps half of its partial sums and adds its partner's copy of them (8, 4, 2,
+// 1 exchanges), then the two lane halves are added.
+__device__ __forceinline__ float colsum16(const float (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+    float a[8], b[4], c[2];
+    const bool h8 = (lane & 8) != 0, h4 = (lane & 4) != 0, h2 = (lane & 2) != 0, h1 = (lane & 1) != 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        a[j] = (h8 ? v[j + 8] : v[j]) + __shfl_xor_sync(0xffffffffu, h8 ? v[j] : v[j + 8], 8);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        b[j] = (h4 ? a[j + 4] : a[j]) + __shfl_xor_sync(0xffffffffu, h4 ? a[j] : a[j + 4], 4);
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+        c[j] = (h2 ? b[j + 2] : b[j]) + __shfl_xor_sync(0xffffffffu, h2 ? b[j] : b[j + 2], 2);
+    const float d = (h1 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h1 ? c[0] : c[1], 1);
+    return d + __shfl_xor_sync(0xffffffffu, d, 16);
+}
+
+struct FtSmem {
+    __nv_bfloat16 T[5][TILE * TILE];
+    float b1[TILE], b2[TILE], w3[TILE];
+    float tgt[TILE], d3[TILE], ypart[4][TILE], lterm[TILE];
+    int valid[TILE];
+    float colred[4][4][TILE];  // [row quarter][db1, db2, dw3, db3][column]
+    float b3;
     uint32_t tmem_base;
     unsigned long long mbar;
 };
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_delta_tc(const uint8_t *params, const float *y, const float *target,
-                                                               int n, const float *z1, const float *z2, float *d1,
-                                                               float *d2, float *d3, int *status) {
+__global__ void __launch_bounds__(FT_THREADS, 1)
+    k_mlp_train_tile(const uint8_t *params, const __nv_bfloat16 *X, const float *target, const int64_t *perm,
+                     long long row0, int n, long long n_all, float *part, double *lpart, int *status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    DtSmem &s = *reinterpret_cast<DtSmem *>(smem_raw);
+    FtSmem &s = *reinterpret_cast<FtSmem *>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long b0 = (long long)blockIdx.x * TILE;
-    const int rows = (int)min((long long)TILE, n - b0);
+    const int tile = blockIdx.x;
+    const long long t0 = (long long)tile * TILE;
+    const int rows = (int)min((long long)TILE, (long long)n - t0);
     const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(params);
-    char *At = reinterpret_cast<char *>(s.A), *Bt = reinterpret_cast<char *>(s.B);
-    if (threadIdx.x < TILE) {
-        const int b = threadIdx.x;
-        s.w3[b] = __bfloat162float(wb[2 * TILE * TILE + b]);
-        float v = 0.f;
-        if (b < rows) {
-            const float tt = target[b0 + b];
-            v = 2.0f * (y[b0 + b] - tt) / ((tt * tt + 7e-5f) * (float)n);
-            d3[b0 + b] = v;
-        }
-        s.d3[b] = v;
-    }
-    // B[i][o] = W2[o][i]: thread per (o, 8 consecutive i)
+    const float *bias = reinterpret_cast<const float *>(params + MB_BIAS_TC);
+    char *T0 = reinterpret_cast<char *>(s.T[0]), *T1 = reinterpret_cast<char *>(s.T[1]);
+    char *T2 = reinterpret_cast<char *>(s.T[2]), *T3 = reinterpret_cast<char *>(s.T[3]);
+    char *T4 = reinterpret_cast<char *>(s.T[4]);
+    auto source = [&](int r) -> long long {  // stencil row of tile row r, or -1
+        if (r >= rows) return -1;
+        const long long k = row0 + t0 + r;
+        const long long src = perm ? perm[k] : k;
+        return (src >= 0 && src < n_all) ? src : -1;
+    };
+    // ---- load: X and X^T, W1, W2, W2^T, vectors, targets.  The 32 lanes of a
+    // warp take 32 rows of one 8-column group: the transposed 2-byte stores
+    // then fall on distinct banks (two lanes per 4-byte word).
     for (int c = threadIdx.x; c < TILE * TILE / 8; c += blockDim.x) {
-        const int o = c >> 4, i8 = (c & 15) * 8;
-        const uint4 v = *reinterpret_cast<const uint4 *>(wb + TILE * TILE + o * TILE + i8);
+        const int r = (c & 31) + 32 * ((c >> 9) & 3), k8 = ((c >> 5) & 15) * 8;
+        const long long src = source(r);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (src >= 0) v = *reinterpret_cast<const uint4 *>(X + src * TILE + k8);
+        *reinterpret_cast<uint4 *>(T0 + tile_off(r, k8)) = v;
         const __nv_bfloat16 *e8 = reinterpret_cast<const __nv_bfloat16 *>(&v);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) *reinterpret_cast<__nv_bfloat16 *>(Bt + tile_off(i8 + e, o)) = e8[e];
+        for (int e = 0; e < 8; ++e) *reinterpret_cast<__nv_bfloat16 *>(T4 + tile_off(k8 + e, r)) = e8[e];
     }
-    __syncthreads();
-    // d2 (FP32 to memory, BF16 into A[b][o])
-    for (int c = threadIdx.x; c < TILE * TILE / 8; c += blockDim.x) {
-        const int b = c >> 4, o8 = (c & 15) * 8;
-        uint32_t h[4];
-        if (b < rows) {
-            float v[8];
+    load_tile(T1, wb, TILE, TILE);
+    load_tile(T2, wb + TILE * TILE, TILE, TILE);
+    for (int c = threadIdx.x; c < TILE * TILE / 8; c += blockDim.x) {  // T3[h][o] = W2[o][h]
+        const int o = (c & 31) + 32 * ((c >> 9) & 3), h8 = ((c >> 5) & 15) * 8;
+        const uint4 v = *reinterpret_cast<const uint4 *>(wb + TILE * TILE + o * TILE + h8);
+        const __nv_bfloat16 *e8 = reinterpret_cast<const __nv_bfloat16 *>(&v);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = s.d3[b] * s.w3[o8 + e] * gelu_grad_tc(z2[(b0 + b) * TILE + o8 + e]);
-            *reinterpret_cast<float4 *>(d2 + (b0 + b) * TILE + o8) = make_float4(v[0], v[1], v[2], v[3]);
-            *reinterpret_cast<float4 *>(d2 + (b0 + b) * TILE + o8 + 4) = make_float4(v[4], v[5], v[6], v[7]);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) h[e] = pack2(v[2 * e], v[2 * e + 1]);
-        } else {
-            h[0] = h[1] = h[2] = h[3] = 0u;
-        }
-        *reinterpret_cast<uint4 *>(At + tile_off(b, o8)) = make_uint4(h[0], h[1], h[2], h[3]);
+        for (int e = 0; e < 8; ++e) *reinterpret_cast<__nv_bfloat16 *>(T3 + tile_off(h8 + e, o)) = e8[e];
+    }
+    if (threadIdx.x < TILE) {
+        const int e = threadIdx.x;
+        s.b1[e] = bias[e];
+        s.b2[e] = bias[TILE + e];
+        s.w3[e] = __bfloat162float(wb[2 * TILE * TILE + e]);
+        const long long src = source(e);
+        s.valid[e] = src >= 0;
+        s.tgt[e] = src >= 0 ? target[src] : 0.f;
     }
     if (threadIdx.x == 0) {
+        s.b3 = bias[2 * TILE];
         mbar_init(&s.mbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem_base)),
-                     "r"(TILE)
+                     "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -426,52 +383,187 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_delta_tc(const uint8_t *p
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s.tmem_base;
-    if (threadIdx.x == 0) {
-        const uint32_t aA = smem_u32(s.A), aB = smem_u32(s.B);
+    const int q4 = warp & 3;                                      // row quarter
+    const uint32_t lane_base = (uint32_t)(32 * q4) << 16;         // this warp's TMEM lanes
+    const int row = 32 * q4 + lane;                               // tile row (and, for dW, output o) of this thread
+    const int cq = warp >> 2;                                     // its column quarter
+    const int col0 = 32 * cq;
+    const uint32_t a0 = smem_u32(T0), a1 = smem_u32(T1), a2 = smem_u32(T2), a3 = smem_u32(T3), a4 = smem_u32(T4);
+    uint32_t phase = 0;
+    bool ok = true;
+    auto mma_group = [&](uint32_t dcol, uint32_t aA, uint32_t aB) {
 #pragma unroll
         for (int kk = 0; kk < TILE / 16; ++kk)
-            tc_mma(tmem, smem_desc(aA + kk * 2 * CORE_K, CORE_K, CORE_MN), smem_desc(aB + kk * 2 * CORE_K, CORE_K, CORE_MN),
-                   kk > 0);
+            tc_mma(tmem + dcol, smem_desc(aA + kk * 2 * CORE_K, CORE_K, CORE_MN),
+                   smem_desc(aB + kk * 2 * CORE_K, CORE_K, CORE_MN), kk > 0);
+    };
+    auto wait_mma = [&]() {
+        if (__syncthreads_or(mbar_wait(&s.mbar, phase) ? 0 : 1)) {
+            if (threadIdx.x == 0) set_status(status, FSL_ETIMEOUT);
+            ok = false;
+        }
+        phase ^= 1;
+        tc_fence_after();
+    };
+    auto handoff = [&]() {  // epilogue writes to shared memory and TMEM reads done before the next MMAs
+        tc_fence_before();
+        proxy_fence();
+        __syncthreads();
+    };
+    auto colsum = [&](float v) {  // sum over the 32 rows of this warp, fixed tree
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
+    // ---- L1
+    if (threadIdx.x == 0) {
+        tc_fence_after();
+        mma_group(0, a0, a1);
         tc_commit(&s.mbar);
     }
-    const bool ok = !__syncthreads_or(mbar_wait(&s.mbar, 0) ? 0 : 1);
-    if (ok) {
-        tc_fence_after();
-        const int b = 32 * (warp & 3) + lane, col0 = 64 * (warp >> 2);
+    wait_mma();
+    if (ok) {  // E1: h1 and h1^T
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
+        for (int cc = 0; cc < 2; ++cc) {
             const int c = col0 + 16 * cc;
             float v[16];
-            tc_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c, v);
-            if (b < rows) {
-                const float *zr = z1 + (b0 + b) * TILE + c;
-                float *dr = d1 + (b0 + b) * TILE + c;
+            tc_ld16(tmem + lane_base + c, v);
+            uint32_t h[8];
 #pragma unroll
-                for (int e = 0; e < 16; e += 4)
-                    *reinterpret_cast<float4 *>(dr + e) =
-                        make_float4(v[e] * gelu_grad_tc(zr[e]), v[e + 1] * gelu_grad_tc(zr[e + 1]),
-                                    v[e + 2] * gelu_grad_tc(zr[e + 2]), v[e + 3] * gelu_grad_tc(zr[e + 3]));
+            for (int e = 0; e < 16; e += 2) {
+                const float ga = gelu_tc(v[e] + s.b1[c + e]), gb = gelu_tc(v[e + 1] + s.b1[c + e + 1]);
+                h[e >> 1] = pack2(ga, gb);
+                *reinterpret_cast<__nv_bfloat16 *>(T1 + tile_off(c + e, row)) = __float2bfloat16_rn(ga);
+                *reinterpret_cast<__nv_bfloat16 *>(T1 + tile_off(c + e + 1, row)) = __float2bfloat16_rn(gb);
+            }
+            *reinterpret_cast<uint4 *>(T0 + tile_off(row, c)) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(T0 + tile_off(row, c + 8)) = make_uint4(h[4], h[5], h[6], h[7]);
+        }
+    }
+    handoff();
+    // ---- L2
+    if (ok && threadIdx.x == 0) {
+        tc_fence_after();
+        mma_group(TILE, a0, a2);
+        tc_commit(&s.mbar);
+    }
+    if (ok) wait_mma();
+    if (ok) {  // E2: y, loss term, d3
+        float yp = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = col0 + 16 * cc;
+            float v[16];
+            tc_ld16(tmem + TILE + lane_base + c, v);
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) {
+                const float za = v[e] + s.b2[c + e], zb = v[e + 1] + s.b2[c + e + 1];
+                yp += gelu_tc(za) * s.w3[c + e] + gelu_tc(zb) * s.w3[c + e + 1];
             }
         }
-    } else if (threadIdx.x == 0) {
-        set_status(status, FSL_ETIMEOUT);
+        s.ypart[cq][row] = yp;
+        __syncthreads();
+        if (cq == 0) {
+            const float y = ((s.ypart[0][row] + s.ypart[1][row]) + s.ypart[2][row]) + s.ypart[3][row] + s.b3;
+            const float tt = s.tgt[row], er = y - tt;
+            const bool vr = s.valid[row] != 0;
+            s.d3[row] = vr ? 2.0f * er / ((tt * tt + 7e-5f) * (float)n) : 0.f;
+            s.lterm[row] = vr ? er * er / (tt * tt + 7e-5f) : 0.f;
+        }
+        __syncthreads();
+        // d2 (FP32 for the vector sums, BF16 into T0 and, transposed, T2)
+        const float d3r = s.d3[row];
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = col0 + 16 * cc;
+            float v[16], dv[16], wv[16];
+            tc_ld16(tmem + TILE + lane_base + c, v);
+            uint32_t h[8];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const float z = v[e] + s.b2[c + e];
+                dv[e] = d3r * s.w3[c + e] * gelu_grad_tc(z);
+                wv[e] = d3r * gelu_tc(z);
+                *reinterpret_cast<__nv_bfloat16 *>(T2 + tile_off(c + e, row)) = __float2bfloat16_rn(dv[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) h[e >> 1] = pack2(dv[e], dv[e + 1]);
+            *reinterpret_cast<uint4 *>(T0 + tile_off(row, c)) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(T0 + tile_off(row, c + 8)) = make_uint4(h[4], h[5], h[6], h[7]);
+            const float sd = colsum16(dv), sw = colsum16(wv);
+            if (lane < 16) {
+                s.colred[q4][1][c + lane] = sd;
+                s.colred[q4][2][c + lane] = sw;
+            }
+        }
+        const float s3 = colsum(d3r);
+        if (lane == 0 && cq == 0) s.colred[q4][3][0] = s3;
+    }
+    handoff();
+    // ---- delta: d2 W2
+    if (ok && threadIdx.x == 0) {
+        tc_fence_after();
+        mma_group(2 * TILE, a0, a3);
+        tc_commit(&s.mbar);
+    }
+    if (ok) wait_mma();
+    if (ok) {  // E3: d1 = (d2 W2) gelu'(z1); d1^T into T3
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = col0 + 16 * cc;
+            float v[16], z[16], dv[16];
+            tc_ld16(tmem + 2 * TILE + lane_base + c, v);
+            tc_ld16(tmem + lane_base + c, z);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                dv[e] = v[e] * gelu_grad_tc(z[e] + s.b1[c + e]);
+                *reinterpret_cast<__nv_bfloat16 *>(T3 + tile_off(c + e, row)) = __float2bfloat16_rn(dv[e]);
+            }
+            const float sd = colsum16(dv);
+            if (lane < 16) s.colred[q4][0][c + lane] = sd;
+        }
+    }
+    handoff();
+    // ---- weight gradients: dW1 = d1^T X, dW2 = d2^T h1
+    if (ok && threadIdx.x == 0) {
+        tc_fence_after();
+        mma_group(3 * TILE, a3, a4);
+        mma_group(TILE, a2, a1);
+        tc_commit(&s.mbar);
+    }
+    if (ok) wait_mma();
+    if (ok) {  // E4: partials of the tile
+        float *P1 = part + (size_t)tile * PART_STRIDE + (size_t)row * TILE;
+        float *P2 = P1 + TILE * TILE;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = col0 + 16 * cc;
+            float v[16];
+            tc_ld16(tmem + 3 * TILE + lane_base + c, v);
+#pragma unroll
+            for (int e = 0; e < 16; e += 4) *reinterpret_cast<float4 *>(P1 + c + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+            tc_ld16(tmem + TILE + lane_base + c, v);
+#pragma unroll
+            for (int e = 0; e < 16; e += 4) *reinterpret_cast<float4 *>(P2 + c + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+        }
+        if (threadIdx.x < TILE) {
+            const int c = threadIdx.x;
+            float *V = part + (size_t)tile * PART_STRIDE + 2 * TILE * TILE;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) V[k * TILE + c] = ((s.colred[0][k][c] + s.colred[1][k][c]) + s.colred[2][k][c]) + s.colred[3][k][c];
+            V[3 * TILE + c] = c == 0 ? ((s.colred[0][3][0] + s.colred[1][3][0]) + s.colred[2][3][0]) + s.colred[3][3][0] : 0.f;
+        }
+        if (threadIdx.x == 0) {
+            double l = 0.0;
+            for (int r = 0; r < TILE; ++r) l += (double)s.lterm[r];
+            lpart[tile] = l;
+        }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TILE) : "memory");
-}
-
-// grad[off + e] = sum over chunks of partial[mat][chunk][e], chunks in order
-__global__ void __launch_bounds__(256) k_mlp_wreduce(const float *partial, int nchunk, float *gW1, float *gW2) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 2 * TILE * TILE) return;
-    const int mat = e / (TILE * TILE), k = e % (TILE * TILE);
-    const float *P = partial + (size_t)mat * nchunk * TILE * TILE + k;
-    float acc = 0.f;
-    for (int c = 0; c < nchunk; ++c) acc += P[(size_t)c * TILE * TILE];
-    (mat == 0 ? gW1 : gW2)[k] = acc;
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 size_t mlp_tc_smem() { return sizeof(TcSmem) + 1024; }
@@ -514,29 +606,19 @@ int launch_mlp_forward_tc(const uint8_t *params, const __nv_bfloat16 *X, int n, 
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
 }
 
-size_t mlp_wgrad_partial_floats(int n) { return (size_t)2 * ((n + TILE - 1) / TILE) * TILE * TILE; }
+size_t mlp_tile_partial_floats(int n) { return (size_t)((n + TILE - 1) / TILE) * PART_STRIDE; }
 
-int launch_mlp_wgrad_tc(const __nv_bfloat16 *X, const float *z1, const float *d1, const float *d2, int n, float *partial,
-                        float *gW1, float *gW2, cudaStream_t s) {
+// one training-step tile kernel per 128 rows of the batch (one CTA per SM at
+// about 170 KB of shared memory and 512 TMEM columns)
+int launch_mlp_train_tile(const uint8_t *params, const __nv_bfloat16 *X, const float *target, const int64_t *perm,
+                          long long row0, int n, long long n_all, float *part, double *lpart, cudaStream_t s) {
     int *st = status_ptr();
     if (!st) return FSL_ECUDA;
-    const int nchunk = (n + TILE - 1) / TILE;
-    const size_t sm = sizeof(WgSmem) + 1024;
-    if (cudaFuncSetAttribute(k_mlp_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    const size_t sm = sizeof(FtSmem) + 1024;
+    if (cudaFuncSetAttribute(k_mlp_train_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return FSL_ECUDA;
-    k_mlp_wgrad_tc<<<dim3(nchunk, 2), TC_THREADS, sm, s>>>(X, z1, d1, d2, n, partial, st);
-    k_mlp_wreduce<<<(2 * TILE * TILE + 255) / 256, 256, 0, s>>>(partial, nchunk, gW1, gW2);
-    return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
-}
-
-int launch_mlp_delta_tc(const uint8_t *params, const float *y, const float *target, int n, const float *z1,
-                        const float *z2, float *d1, float *d2, float *d3, cudaStream_t s) {
-    int *st = status_ptr();
-    if (!st) return FSL_ECUDA;
-    const size_t sm = sizeof(DtSmem) + 1024;
-    if (cudaFuncSetAttribute(k_mlp_delta_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-        return FSL_ECUDA;
-    k_mlp_delta_tc<<<(n + TILE - 1) / TILE, TC_THREADS, sm, s>>>(params, y, target, n, z1, z2, d1, d2, d3, st);
+    k_mlp_train_tile<<<(n + TILE - 1) / TILE, FT_THREADS, sm, s>>>(params, X, target, perm, row0, n, n_all, part, lpart,
+                                                                   st);
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
 }
 

@@ -62,7 +62,7 @@ def test_workspace_size_and_validation_without_gpu(libpath):
     # bad arguments are rejected before any device work (the pointers below are never dereferenced)
     L = fsl.lib()
     assert L.fsl_mlp_epoch_workspace(0) == 0
-    assert L.fsl_mlp_epoch_workspace(4096) >= L.fsl_mlp_train_workspace(4096) + 4096 * (256 + 4)
+    assert L.fsl_mlp_epoch_workspace(4096) >= L.fsl_mlp_train_workspace(4096) > 0
     fake = [ctypes.c_void_p(1 << 20)] * 7
     def epoch(n, batch, lr=1e-3, step0=0, ptrs=fake, ws=ctypes.c_void_p(1 << 20)):
         return L.fsl_mlp_train_epoch(*ptrs, n, batch, lr, step0, None, ws, None)
