@@ -21,6 +21,7 @@ struct Adj {
     float *jac;          // [cap][JAC_STRIDE]
     float *jval;         // [cap] kappa value of the Jacobian pass
     int *dlist;          // wlist positions whose Jacobian is redone in FP64
+    int *glist;          // wlist positions whose Jacobian takes the dual-number path
     float4 *nj;          // [cap][125] d(n, a)/dphi over the 5x5x5 window of each interface cell
     const float *fb_in;  // adjoint of the post-collision PDFs at t+1 [19 N]
     float *fb_out;       // adjoint of the post-collision PDFs at t   [19 N]

@@ -232,7 +232,8 @@ int record_graph(fsl_ctx *c, int parity) {
 constexpr int ADJ_MAX_PARTIALS = 4096;
 
 struct AdjLayout {
-    size_t wcounts, wlist, widx, wseg, wscr, ckpt, slot, kn, fb0, fb1, gb, mb, pb, kb, jac, jval, dlist, nj, part, acc, total;
+    size_t wcounts, wlist, widx, wseg, wscr, ckpt, slot, kn, fb0, fb1, gb, mb, pb, kb, jac, jval, dlist, glist, nj, part, acc,
+        total;
     size_t state_bytes;  // one (f', m, phi) record
     size_t kn_bytes;     // one (kappa, normal) record
     int nseg_ckpt;
@@ -262,6 +263,7 @@ AdjLayout adj_layout(const fsl_params &p, int W, int K, int cap) {
     A.jac = o; o += up((size_t)cap * JAC_STRIDE * sizeof(float));
     A.jval = o; o += up((size_t)cap * sizeof(float));
     A.dlist = o; o += up((size_t)cap * sizeof(int));
+    A.glist = o; o += up((size_t)cap * sizeof(int));
     A.nj = o; o += up((size_t)cap * 125 * sizeof(float4));
     A.part = o; o += up(2 * ADJ_MAX_PARTIALS * sizeof(double));
     A.acc = o; o += up(2 * sizeof(double));
@@ -312,6 +314,7 @@ Adj adj_args(char *ws, const AdjLayout &A, int cap) {
     a.jac = reinterpret_cast<float *>(ws + A.jac);
     a.jval = reinterpret_cast<float *>(ws + A.jval);
     a.dlist = reinterpret_cast<int *>(ws + A.dlist);
+    a.glist = reinterpret_cast<int *>(ws + A.glist);
     a.nj = reinterpret_cast<float4 *>(ws + A.nj);
     a.gb = reinterpret_cast<float *>(ws + A.gb);
     a.mb = reinterpret_cast<float *>(ws + A.mb);

@@ -31,11 +31,12 @@
 //                 sum_x kbar(x) dkappa_x/dphi_y, and dL/dtheta
 //   k_adj_accum   fixed-order sum of the per-block sigma and theta partials
 // Gathers (not scatters) keep every sum in a fixed order: the result is
-// bit-reproducible.  The curvature Jacobian rows come from forward-mode dual
-// numbers through the same per-cell code as the forward LSQR fit
-// (curv_common.cuh): one warp per interface cell, one seed (a window cell's
-// phi, or theta) per lane, the fill levels and flags of the 7x7x7 window in
-// shared memory.
+// bit-reproducible.  The curvature Jacobian rows: the normal and PLIC offset
+// sensitivities by forward-mode dual numbers through the same per-cell code
+// as k_normals (one seed per lane), the fit's sensitivities by one reverse
+// sweep of the FP32 normal equations, or, for contact-line and degenerate
+// fits, by dual numbers through lsqr_core (curv_common.cuh), one seed per
+// thread.
 #include "adjoint.cuh"
 #include "curv_common.cuh"
 
@@ -232,13 +233,18 @@ __device__ __forceinline__ void collide_adj(const float g[Q], const float fb[Q],
 //                 window around j (Parker-Youngs stencil, obstacle reflection,
 //                 PLIC offset by the implicit function theorem); dual numbers
 //                 through the same code as k_normals, one seed per lane
-//   k_kappa_jac   per interface cell x: dkappa_x/d(n_j, a_j) for the four
+//   k_kappa_rev   per interface cell x: dkappa_x/d(n_j, a_j) for the four
 //                 inputs of each interface cell j of the 3x3x3 neighbourhood
-//                 and dkappa_x/dtheta (dual numbers through lsqr_core with the
-//                 stored normals as values, one seed per lane), then the
-//                 chain rule dkappa_x/dphi_y = sum_j sum_c
-//                 dkappa_x/d(n_j,a_j)_c d(n_j,a_j)_c/dphi_y
-//                 into the row of x (7x7x7 window slots, theta last).
+//                 by one reverse sweep of the fit (the full model without
+//                 contact rows), then the chain rule dkappa_x/dphi_y =
+//                 sum_j sum_c dkappa_x/d(n_j,a_j)_c d(n_j,a_j)_c/dphi_y
+//                 into the row of x (7x7x7 window slots, theta last)
+//   k_kappa_gen   the cells the sweep does not cover (contact rows, the
+//                 centre constraint, fewer than five rows, a fit that is not
+//                 positive definite or ill conditioned): the same
+//                 sensitivities and dkappa_x/dtheta by dual numbers through
+//                 lsqr_core with the stored normals as values, one seed per
+//                 thread; the same chain rule.
 // A cell whose FP32 fit is ill conditioned (cond^2 above fp64_cond, as
 // k_lsqr_slow decides) is listed and its second stage redone in Dual<double>.
 
@@ -323,23 +329,26 @@ __global__ void __launch_bounds__(JAC_WARPS * 32) k_normal_jac(Dev d, Adj a) {
     }
 }
 
-// Accessor of lsqr_core over the grid with the stored normals as values and
-// one seeded input: component c of (n_j, a_j) of the neighbour j at 3x3x3
-// slot sj, or theta.
+// Accessor of lsqr_core over a cell's neighbourhood staged in shared memory
+// (flags of the 5x5x5 block, stored normals of the 3x3x3 block) with the
+// stored normals as values and one seeded input: component c of (n_j, a_j)
+// of the neighbour j at 3x3x3 slot sj, or theta.
 struct SeedAcc {
     const Dev &d;
-    int x, y, z;
+    const uint8_t *fl;  // slot ((dz+2)*5 + dy+2)*5 + dx+2
+    const float4 *nm;   // slot (dz+1)*9 + (dy+1)*3 + dx+1
     int sj, sc;
     bool sth;
     __device__ __forceinline__ uint8_t flag(int dx, int dy, int dz) const {
-        return d.flags[nbr_index(d, x, y, z, dx, dy, dz)];
+        return fl[((dz + 2) * 5 + (dy + 2)) * 5 + (dx + 2)];
     }
     template <typename T>
     __device__ __forceinline__ bool normal(int dx, int dy, int dz, T n[3], T &a) const {
         using S = typename scalar_of<T>::type;
-        const float4 q4 = d.normal[nbr_index(d, x, y, z, dx, dy, dz)];
+        const int t = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+        const float4 q4 = nm[t];
         if (q4.x == 0.f && q4.y == 0.f && q4.z == 0.f) return false;
-        const bool me = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1) == sj;
+        const bool me = t == sj;
         n[0] = T((S)q4.x, (me && sc == 0) ? S(1) : S(0), 0);
         n[1] = T((S)q4.y, (me && sc == 1) ? S(1) : S(0), 0);
         n[2] = T((S)q4.z, (me && sc == 2) ? S(1) : S(0), 0);
@@ -356,98 +365,378 @@ struct SeedAcc {
 
 constexpr int KJ_SEEDS = 27 * 4 + 1;  // (n_j, a_j) of each 3x3x3 cell, theta
 
-template <typename T, bool FROM_LIST>
-__global__ void __launch_bounds__(JAC_WARPS * 32) k_kappa_jac(Dev d, Adj a) {
+// ---- reverse-mode sensitivities of the FP32 fit ----------------------------------
+// Butterfly sum over the warp; both partners of every stage add the same two
+// operands, so all lanes end with the same bits.
+__device__ __forceinline__ float warp_allsum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ constexpr int pk5(int r, int c) { return r * 5 - r * (r - 1) / 2 + (c - r); }
+
+// Cholesky factor R (upper, packed) of the packed symmetric 5x5 matrix G;
+// pd: every pivot positive; cond = (max / min diagonal of R)^2, the condition
+// estimate of G the forward fit uses.
+__device__ __forceinline__ void chol5(const float G[15], float R[15], bool &pd, float &cond) {
+    float dmax = 0.f, dmin = 3.0e38f;
+    pd = true;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+#pragma unroll
+        for (int c = r; c < 5; ++c) {
+            float sum = G[pk5(r, c)];
+#pragma unroll
+            for (int k = 0; k < r; ++k) sum -= R[pk5(k, r)] * R[pk5(k, c)];
+            if (c == r) {
+                pd = pd && sum > 0.f;
+                const float dd = sqrtf(fmaxf(sum, 1e-30f));
+                R[pk5(r, r)] = dd;
+                dmax = fmaxf(dmax, dd);
+                dmin = fminf(dmin, dd);
+            } else {
+                R[pk5(r, c)] = sum / R[pk5(r, r)];
+            }
+        }
+    }
+    cond = (dmax / dmin) * (dmax / dmin);
+}
+
+// x = G^-1 b with G = R^T R
+__device__ __forceinline__ void chol5_solve(const float R[15], const float b[5], float x[5]) {
+    float y[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        float sum = b[r];
+#pragma unroll
+        for (int k = 0; k < r; ++k) sum -= R[pk5(k, r)] * y[k];
+        y[r] = sum / R[pk5(r, r)];
+    }
+#pragma unroll
+    for (int r = 4; r >= 0; --r) {
+        float sum = y[r];
+#pragma unroll
+        for (int k = r + 1; k < 5; ++k) sum -= R[pk5(r, k)] * x[k];
+        x[r] = sum / R[pk5(r, r)];
+    }
+}
+
+// dkappa/d(n_t, a_t) of the centre cell's LSQR curvature for every slot t of
+// its 3x3x3 block, by one reverse sweep instead of one dual evaluation per
+// input.  Lane t < 27 holds slot t (flags fj, stored normal and offset q4;
+// centre 13).  The fit is the unconstrained full model (Sec. II.C): rows
+// (u^2, v^2, uv, u, v) and right-hand side f of the PLIC points in the frame
+// (t_u, t_v, n) of the centre normal, solved by the normal equations G x = r,
+// kappa by Eq. (anacurv).  The sweep, with bars for sensitivities of kappa:
+//   xbar = dkappa/d(A, B, C, H, I), lambda = G^-1 xbar,
+//   per row j (residual e_j = f_j - row_j.x):
+//     rowbar_j = e_j lambda - (row_j.lambda) x,  fbar_j = row_j.lambda,
+//   then through u = d.t_u, v = d.t_v, f = d.n with d = o_j + a_j n_j - a n,
+//   and the centre's frame (t_u = w / |w|, t_v = n x t_u) and origin a n.
+// Returns false (the same on every lane) where the cell needs the general
+// path: a contact-line cell in the block (gradient rows or the centre
+// constraint), a zero centre normal, fewer than five rows, or normal
+// equations that are not positive definite or worse conditioned than
+// fp64_cond.  theta does not enter such a fit.
+__device__ bool kappa_reverse(int lane, uint8_t fj, float4 q4, float fp64_cond, float &kap, float4 &g4) {
+    const unsigned full = 0xffffffffu;
+    const bool isif = lane < 27 && (fj & T_IF);
+    if (__any_sync(full, isif && (fj & B_NEAR))) return false;
+    float4 c4;
+    c4.x = __shfl_sync(full, q4.x, 13);
+    c4.y = __shfl_sync(full, q4.y, 13);
+    c4.z = __shfl_sync(full, q4.z, 13);
+    c4.w = __shfl_sync(full, q4.w, 13);
+    if (c4.x == 0.f && c4.y == 0.f && c4.z == 0.f) return false;
+    FastFrame F;
+    lsqr_fast_frame(c4, F);
+    const bool row = isif && lane != 13 && !(q4.x == 0.f && q4.y == 0.f && q4.z == 0.f);
+    const float dv[3] = {(float)(lane % 3 - 1) + q4.w * q4.x - F.p[0], (float)((lane / 3) % 3 - 1) + q4.w * q4.y - F.p[1],
+                         (float)(lane / 9 - 1) + q4.w * q4.z - F.p[2]};
+    const float u = dot3(dv, F.tu), v = dot3(dv, F.tv);
+    const float fr = row ? dot3(dv, F.n) : 0.f;
+    float a5[5] = {u * u, v * v, u * v, u, v};
+#pragma unroll
+    for (int c = 0; c < 5; ++c) a5[c] = row ? a5[c] : 0.f;
+    float G[15], rv[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+#pragma unroll
+        for (int c = r; c < 5; ++c) G[pk5(r, c)] = warp_allsum(a5[r] * a5[c]);
+        rv[r] = warp_allsum(a5[r] * fr);
+    }
+    const int m = __popc(__ballot_sync(full, row));
+    float R[15], cond;
+    bool pd;
+    chol5(G, R, pd, cond);
+    if (!(m >= 5 && pd && !(cond > fp64_cond))) return false;
+    float x[5];
+    chol5_solve(R, rv, x);
+    const float A = x[0], B = x[1], C = x[2], H = x[3], I = x[4];
+    const float g = 1.0f + H * H + I * I, D = g * sqrtf(g);
+    const float Nn = A * (1.0f + I * I) + B * (1.0f + H * H) - C * H * I;
+    kap = Nn / D;
+    const float xb[5] = {(1.0f + I * I) / D, (1.0f + H * H) / D, -H * I / D,
+                         (2.0f * B * H - C * I - 3.0f * Nn * H / g) / D, (2.0f * A * I - C * H - 3.0f * Nn * I / g) / D};
+    float lam[5];
+    chol5_solve(R, xb, lam);
+    // this lane's row
+    float e = fr, rl = 0.f;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        e -= a5[c] * x[c];
+        rl += a5[c] * lam[c];
+    }
+    float rb[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) rb[c] = row ? e * lam[c] - rl * x[c] : 0.f;
+    const float ub = 2.0f * u * rb[0] + v * rb[2] + rb[3];
+    const float vb = 2.0f * v * rb[1] + u * rb[2] + rb[4];
+    const float fb = row ? rl : 0.f;
+    float db[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) db[c] = ub * F.tu[c] + vb * F.tv[c] + fb * F.n[c];
+    g4 = row ? make_float4(q4.w * db[0], q4.w * db[1], q4.w * db[2], q4.x * db[0] + q4.y * db[1] + q4.z * db[2])
+             : make_float4(0.f, 0.f, 0.f, 0.f);
+    // the centre's frame and origin
+    float tub[3], tvb[3], nb[3], pb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        tub[c] = warp_allsum(row ? ub * dv[c] : 0.f);
+        tvb[c] = warp_allsum(row ? vb * dv[c] : 0.f);
+        nb[c] = warp_allsum(row ? fb * dv[c] : 0.f);
+        pb[c] = -warp_allsum(db[c]);
+    }
+    const float *n = F.n, *tu = F.tu;
+    nb[0] += tu[1] * tvb[2] - tu[2] * tvb[1];  // t_v = n x t_u
+    nb[1] += tu[2] * tvb[0] - tu[0] * tvb[2];
+    nb[2] += tu[0] * tvb[1] - tu[1] * tvb[0];
+    tub[0] += tvb[1] * n[2] - tvb[2] * n[1];
+    tub[1] += tvb[2] * n[0] - tvb[0] * n[2];
+    tub[2] += tvb[0] * n[1] - tvb[1] * n[0];
+    int k = 0;  // the frame's case, as lsqr_fast_frame picks it
+    if (fabsf(n[1]) < fabsf(n[0])) k = 1;
+    if (fabsf(n[2]) < fabsf(n[k])) k = 2;
+    float wv[3];
+    if (k == 0) { wv[0] = 0.f; wv[1] = -n[2]; wv[2] = n[1]; }
+    else if (k == 1) { wv[0] = n[2]; wv[1] = 0.f; wv[2] = -n[0]; }
+    else { wv[0] = -n[1]; wv[1] = n[0]; wv[2] = 0.f; }
+    const float wl = sqrtf(dot3(wv, wv)), tt = dot3(tu, tub);
+    float wb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) wb[c] = (tub[c] - tu[c] * tt) / wl;
+    if (k == 0) { nb[2] -= wb[1]; nb[1] += wb[2]; }
+    else if (k == 1) { nb[2] += wb[0]; nb[0] -= wb[2]; }
+    else { nb[1] -= wb[0]; nb[0] += wb[1]; }
+    const float ab = dot3(pb, n);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nb[c] += c4.w * pb[c];
+    if (lane == 13) g4 = make_float4(nb[0], nb[1], nb[2], ab);
+    return true;
+}
+
+// Chain rule into the row of x: each used cell j of the 3x3x3 block adds
+// sum_c dkappa_x/d(n_j,a_j)_c d(n_j,a_j)_c/dphi over the 5x5x5 window around j
+// (a block of the 7x7x7 row) into acc7.  K holds the four sensitivities of the
+// cell at 3x3x3 slot tj from K[pos[tj]]; the slots tj0, tj0 + step, ... are
+// this warp's, in ascending order, so every entry sums in a fixed order.
+__device__ __forceinline__ void chain_rows(const Adj &a, const int *idx, const int *pos, const float *K, float *acc7,
+                                           int tj0, int step, int lane) {
+    for (int sl = lane; sl < JAC_CELLS; sl += 32) acc7[sl] = 0.f;
+    __syncwarp();
+    for (int tj = tj0; tj < 27; tj += step) {
+        const int jk = idx[tj];
+        if (jk < 0) continue;
+        const int p = pos[tj];
+        const float k0 = K[p], k1 = K[p + 1], k2 = K[p + 2], k3 = K[p + 3];
+        const float4 *nrow = a.nj + (size_t)jk * NJ_CELLS;
+        const int jx = tj % 3, jy = (tj / 3) % 3, jz = tj / 9;  // 7x7x7 slot of the corner of j's 5x5x5 window
+        float4 v[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int r = lane + 32 * h;
+            v[h] = r < NJ_CELLS ? nrow[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int r = lane + 32 * h;
+            if (r < NJ_CELLS) {
+                const int sl = ((jz + r / 25) * 7 + (jy + (r / 5) % 5)) * 7 + (jx + r % 5);
+                acc7[sl] += k0 * v[h].x + k1 * v[h].y + k2 * v[h].z + k3 * v[h].w;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// The seeds of cell x (lanes of one warp, lane t < 27 holding 3x3x3 slot t
+// with flags fj and stored normal q4): the four inputs of every interface
+// cell of the block with a nonzero normal and a window-list position, then
+// theta.  Fills idx / pos (per slot) and seed (codes 4 t + c, 108 = theta);
+// returns the number of seeds.
+__device__ __forceinline__ int seed_list(const Adj &a, int lane, int jw, uint8_t fj, float4 q4, int *idx, int *pos,
+                                         uint8_t *seed) {
+    bool use = false;
+    int jdx = -1;
+    if (lane < 27) {
+        use = (fj & T_IF) && !(q4.x == 0.f && q4.y == 0.f && q4.z == 0.f);
+        jdx = use ? a.widx[jw] : -1;
+        use = use && jdx >= 0 && jdx < a.cap;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, use);
+    const int nu = __popc(m);
+    if (lane < 27) {
+        const int p = use ? 4 * __popc(m & ((1u << lane) - 1u)) : -1;
+        idx[lane] = use ? jdx : -1;
+        pos[lane] = p;
+        if (use)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) seed[p + c] = (uint8_t)(lane * 4 + c);
+    }
+    if (lane == 0) seed[4 * nu] = (uint8_t)(27 * 4);
+    return 4 * nu + 1;
+}
+
+// Warp per interface cell of the window: the reverse sweep; cells it does
+// not cover go to the general list (C_ADJGEN).
+__global__ void __launch_bounds__(JAC_WARPS * 32) k_kappa_rev(Dev d, Adj a) {
     __shared__ uint8_t sseed[JAC_WARPS][KJ_SEEDS + 3];
     __shared__ float sK[JAC_WARPS][KJ_SEEDS + 3];
     __shared__ int sidx[JAC_WARPS][27];  // window-list position of the 3x3x3 cells used, -1 otherwise
-    __shared__ int spos[JAC_WARPS][27];  // their first seed in sK
+    __shared__ int spos[JAC_WARPS][27];  // their first entry in sK
+    __shared__ float sacc[JAC_WARPS][JAC_CELLS + 1];
     int cnt[1];
-    block_counts<1>(d.counts, {FROM_LIST ? C_ADJ64 : C_IF0}, cnt);
-    const int n = FROM_LIST ? cnt[0] : min(cnt[0], a.cap);
+    block_counts<1>(d.counts, {C_IF0}, cnt);
+    const int n = min(cnt[0], a.cap);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-    for (int t = gw; t < n; t += nwarps) {
-        const int k = FROM_LIST ? a.dlist[t] : t;
+    for (int k = gw; k < n; k += nwarps) {
+        const int i = a.wlist[k];
+        int x, y, z;
+        cell_coords(d, i, x, y, z);
+        uint8_t fj = 0;
+        float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        int jw = 0;
+        if (lane < 27) {
+            jw = nbr_index(d, x, y, z, lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1);
+            fj = d.flags[jw];
+            q4 = d.normal[jw];
+        }
+        const int ns = seed_list(a, lane, jw, fj, q4, sidx[w], spos[w], sseed[w]);
+        __syncwarp();
+        float kr;
+        float4 g4;
+        if (!kappa_reverse(lane, fj, q4, d.fp64_cond, kr, g4)) {
+            if (lane == 0) a.glist[atomicAdd(d.counts + C_ADJGEN, 1)] = k;
+            __syncwarp();
+            continue;
+        }
+        if (lane < 27 && sidx[w][lane] >= 0) {
+            const int p = spos[w][lane];
+            sK[w][p] = g4.x;
+            sK[w][p + 1] = g4.y;
+            sK[w][p + 2] = g4.z;
+            sK[w][p + 3] = g4.w;
+        }
+        if (lane == 0) {
+            sK[w][ns - 1] = 0.f;  // theta enters no such fit
+            a.jval[k] = kr;
+        }
+        __syncwarp();
+        chain_rows(a, sidx[w], spos[w], sK[w], sacc[w], 0, 1, lane);
+        float *jrow = a.jac + (size_t)k * JAC_STRIDE;
+        for (int sl = lane; sl < JAC_CELLS; sl += 32) jrow[sl] = sacc[w][sl];
+        if (lane == 0) jrow[JAC_CELLS] = sK[w][ns - 1];
+        __syncwarp();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cnt[0] > a.cap) set_status(d.status, FSL_ECAPACITY);
+}
+
+// Block per cell of the general list (contact-line cells, degenerate or
+// ill-conditioned fits) in FP32 duals, or of the FP64 list in FP64 duals:
+// the neighbourhood staged in shared memory, one dual evaluation of
+// lsqr_core per seed (at most 109 seeds, one per thread), the chain rule
+// split over the warps by slot (partial rows summed in warp order).  An FP32
+// fit that is ill conditioned (cond^2 above fp64_cond, as k_lsqr_slow
+// decides) moves the cell to the FP64 list.
+constexpr int GEN_WARPS = 4;
+static_assert(GEN_WARPS * 32 >= KJ_SEEDS, "one seed per thread");
+
+template <typename T, bool FP64>
+__global__ void __launch_bounds__(GEN_WARPS * 32) k_kappa_gen(Dev d, Adj a) {
+    __shared__ uint8_t sfl[128];
+    __shared__ float4 snm[27];
+    __shared__ uint8_t sseed[KJ_SEEDS + 3];
+    __shared__ float sK[KJ_SEEDS + 3];
+    __shared__ int sidx[27], spos[27];
+    __shared__ int sns;
+    __shared__ float sacc[GEN_WARPS][JAC_CELLS + 1];
+    int cnt[1];
+    block_counts<1>(d.counts, {FP64 ? C_ADJ64 : C_ADJGEN}, cnt);
+    const int n = min(cnt[0], a.cap);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const int k = FP64 ? a.dlist[t] : a.glist[t];
         const int i = a.wlist[k];
         int x, y, z;
         cell_coords(d, i, x, y, z);
         const uint8_t fi = d.flags[i];
-        // seeds: the four inputs of every interface cell of the 3x3x3
-        // neighbourhood with a nonzero normal, then theta
-        bool use = false;
-        int jdx = -1;
-        if (lane < 27) {
-            const int j = nbr_index(d, x, y, z, lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1);
-            const float4 q4 = d.normal[j];
-            use = (d.flags[j] & T_IF) && !(q4.x == 0.f && q4.y == 0.f && q4.z == 0.f);
-            jdx = use ? a.widx[j] : -1;
-            use = use && jdx >= 0 && jdx < a.cap;
+        if (threadIdx.x < 125) {
+            const int e = threadIdx.x;
+            sfl[e] = d.flags[nbr_index(d, x, y, z, e % 5 - 2, (e / 5) % 5 - 2, e / 25 - 2)];
         }
-        const unsigned m = __ballot_sync(0xffffffffu, use);
-        const int nu = __popc(m);
-        if (lane < 27) {
-            const int p = use ? 4 * __popc(m & ((1u << lane) - 1u)) : -1;
-            sidx[w][lane] = use ? jdx : -1;
-            spos[w][lane] = p;
-            if (use)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) sseed[w][p + c] = (uint8_t)(lane * 4 + c);
-        }
-        if (lane == 0) sseed[w][4 * nu] = (uint8_t)(27 * 4);
-        const int ns = 4 * nu + 1;
-        __syncwarp();
-        bool redo = false;
-        for (int base = 0; base < ns; base += 32) {
-            const int idx = base + lane;
-            const int code = idx < ns ? (int)sseed[w][idx] : -1;
-            const SeedAcc acc{d, x, y, z, code >= 0 && code < 108 ? code >> 2 : -1, code & 3, code == 108};
-            T cond;
-            const T kap = lsqr_core<T>(acc, fi, cond);
-            if (!FROM_LIST && (float)(cond.v * cond.v) > d.fp64_cond) {
-                redo = true;  // same value on every lane
-                break;
+        if (w == 0) {
+            uint8_t fj = 0;
+            float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            int jw = 0;
+            if (lane < 27) {
+                jw = nbr_index(d, x, y, z, lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1);
+                fj = d.flags[jw];
+                q4 = d.normal[jw];
+                snm[lane] = q4;
             }
-            if (idx < ns) sK[w][idx] = (float)kap.d;
-            if (base == 0 && lane == 0) a.jval[k] = (float)kap.v;
+            const int ns = seed_list(a, lane, jw, fj, q4, sidx, spos, sseed);
+            if (lane == 0) sns = ns;
         }
-        if (redo) {
-            if (lane == 0) a.dlist[atomicAdd(d.counts + C_ADJ64, 1)] = k;
-            __syncwarp();
+        __syncthreads();
+        const int ns = sns;
+        const int code = (int)threadIdx.x < ns ? (int)sseed[threadIdx.x] : -1;
+        const SeedAcc acc{d, sfl, snm, code >= 0 && code < 108 ? code >> 2 : -1, code & 3, code == 108};
+        T cond;
+        const T kap = lsqr_core<T>(acc, fi, cond);
+        if ((int)threadIdx.x < ns) sK[threadIdx.x] = (float)kap.d;
+        if (threadIdx.x == 0) a.jval[k] = (float)kap.v;
+        // the condition of the fit does not depend on the seed: the same on every thread
+        if (__syncthreads_or(!FP64 && (float)(cond.v * cond.v) > d.fp64_cond)) {
+            if (threadIdx.x == 0) a.dlist[atomicAdd(d.counts + C_ADJ64, 1)] = k;
             continue;
         }
-        __syncwarp();
-        // chain rule into the row of x
+        chain_rows(a, sidx, spos, sK, sacc[w], w, GEN_WARPS, lane);
+        __syncthreads();
         float *jrow = a.jac + (size_t)k * JAC_STRIDE;
-        for (int sl = lane; sl < JAC_CELLS; sl += 32) {
-            const int ox = sl % 7 - 3, oy = (sl / 7) % 7 - 3, oz = sl / 49 - 3;
-            if (!(d.flags[nbr_index(d, x, y, z, ox, oy, oz)] & T_IF)) continue;
-            float acc = 0.f;
-            for (int tj = 0; tj < 27; ++tj) {
-                const int jk = sidx[w][tj];
-                if (jk < 0) continue;
-                const int rx = ox - (tj % 3 - 1), ry = oy - ((tj / 3) % 3 - 1), rz = oz - (tj / 9 - 1);
-                if (rx < -2 || rx > 2 || ry < -2 || ry > 2 || rz < -2 || rz > 2) continue;
-                const float4 v = a.nj[(size_t)jk * NJ_CELLS + ((rz + 2) * 5 + (ry + 2)) * 5 + (rx + 2)];
-                const int p = spos[w][tj];
-                acc += sK[w][p] * v.x + sK[w][p + 1] * v.y + sK[w][p + 2] * v.z + sK[w][p + 3] * v.w;
-            }
-            jrow[sl] = acc;
+        for (int sl = threadIdx.x; sl < JAC_CELLS; sl += blockDim.x) {
+            float v = sacc[0][sl];
+#pragma unroll
+            for (int ww = 1; ww < GEN_WARPS; ++ww) v += sacc[ww][sl];
+            jrow[sl] = v;
         }
-        if (lane == 0) jrow[JAC_CELLS] = sK[w][ns - 1];
-        __syncwarp();
+        if (threadIdx.x == 0) jrow[JAC_CELLS] = sK[ns - 1];
+        __syncthreads();  // shared memory is reused by the next cell
     }
-    if (!FROM_LIST && blockIdx.x == 0 && threadIdx.x == 0 && cnt[0] > a.cap) set_status(d.status, FSL_ECAPACITY);
 }
 
 void launch_kappa_jacobian(const Dev &d, const Adj &a, cudaStream_t s) {
     static const int gn = list_blocks((const void *)k_normal_jac, JAC_WARPS * 32, 4);
-    static const int g = list_blocks((const void *)k_kappa_jac<Dual<float>, false>, JAC_WARPS * 32, 4);
-    static const int g64 = list_blocks((const void *)k_kappa_jac<Dual<double>, true>, JAC_WARPS * 32, 1);
+    static const int g = list_blocks((const void *)k_kappa_rev, JAC_WARPS * 32, 4);
+    static const int g32 = list_blocks((const void *)k_kappa_gen<Dual<float>, false>, GEN_WARPS * 32, 4);
+    static const int g64 = list_blocks((const void *)k_kappa_gen<Dual<double>, true>, GEN_WARPS * 32, 2);
     cudaMemsetAsync(d.counts + C_ADJ64, 0, sizeof(int), s);
+    cudaMemsetAsync(d.counts + C_ADJGEN, 0, sizeof(int), s);
     k_normal_jac<<<gn, JAC_WARPS * 32, 0, s>>>(d, a);
-    k_kappa_jac<Dual<float>, false><<<g, JAC_WARPS * 32, 0, s>>>(d, a);
-    k_kappa_jac<Dual<double>, true><<<g64, JAC_WARPS * 32, 0, s>>>(d, a);
+    k_kappa_rev<<<g, JAC_WARPS * 32, 0, s>>>(d, a);
+    k_kappa_gen<Dual<float>, false><<<g32, GEN_WARPS * 32, 0, s>>>(d, a);
+    k_kappa_gen<Dual<double>, true><<<g64, GEN_WARPS * 32, 0, s>>>(d, a);
 }
 
 // ---- reverse of the stream-collide, boundary condition and mass exchange ---------

@@ -7,8 +7,9 @@
 //              (Sec. II.C): FP32 normal equations where that is safe, else
 //              streaming Givens QR in registers, re-solved in FP64 when R is
 //              ill conditioned.
-//   k_fd       finite-difference curvature -1/2 div(n) of the K8-smoothed fill
+//   k_fd_warp  finite-difference curvature -1/2 div(n) of the K8-smoothed fill
 //              level with wetting normals at obstacle cells (Sec. II.A).
+//   k_tr       triangle-fan curvature of the PLIC points (Sec. II.B).
 // The per-cell arithmetic is in curv_common.cuh.
 #include "curv_common.cuh"
 
@@ -166,7 +167,7 @@ __device__ __forceinline__ float k8w(int dx, int dy, int dz) {
 
 // K8-smoothed fill level (eps = 2 on the 3x3x3 stencil, normalised by the
 // discrete weight sum 3.6796875) at a non-obstacle cell
-__device__ float smooth_at(const Dev &d, int x, int y, int z) {
+__device__ __noinline__ float smooth_at(const Dev &d, int x, int y, int z) {
     float s = 0.f;
     for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy)
@@ -175,7 +176,7 @@ __device__ float smooth_at(const Dev &d, int x, int y, int z) {
 }
 
 // smoothed field at any cell; obstacle cells reflect the smoothed field
-__device__ float smooth_ext(const Dev &d, int x, int y, int z) {
+__device__ __noinline__ float smooth_ext(const Dev &d, int x, int y, int z) {
     x = wrap(x, d.nx);
     y = wrap(y, d.ny);
     z = wrap(z, d.nz);
@@ -198,7 +199,7 @@ __device__ void unit_or_zero(float n[3]) {
 
 // unit normal of the smoothed field; at obstacle cells the wetting normal of
 // Eq. (contactNormal) from the neighbour x_b most aligned with the outward wall normal
-__device__ void fd_normal(const Dev &d, int x, int y, int z, float n[3]) {
+__device__ __noinline__ void fd_normal(const Dev &d, int x, int y, int z, float n[3]) {
     x = wrap(x, d.nx);
     y = wrap(y, d.ny);
     z = wrap(z, d.nz);
@@ -239,39 +240,18 @@ __device__ void fd_normal(const Dev &d, int x, int y, int z, float n[3]) {
     for (int k = 0; k < 3; ++k) n[k] = w[k] * d.cos_theta + nt[k] * d.sin_theta;
 }
 
-__global__ void __launch_bounds__(LIST_THREADS) k_fd(Dev d, float *kappa_out) {
-    int cnt[1];
-    block_counts<1>(d.counts, {d.cif}, cnt);
-    const int n = cnt[0];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int i = d.iflist[k];
-        int x, y, z;
-        cell_coords(d, i, x, y, z);
-        float np[3], nm[3], div = 0.f;
-        fd_normal(d, x + 1, y, z, np);
-        fd_normal(d, x - 1, y, z, nm);
-        div += np[0] - nm[0];
-        fd_normal(d, x, y + 1, z, np);
-        fd_normal(d, x, y - 1, z, nm);
-        div += np[1] - nm[1];
-        fd_normal(d, x, y, z + 1, np);
-        fd_normal(d, x, y, z - 1, nm);
-        div += np[2] - nm[2];
-        kappa_out[i] = -0.25f * div;
-    }
-}
-
 // FD curvature, one warp per interface cell: the fill levels of the 7^3
 // block around the cell are staged in shared memory once, the lanes share the
 // 5^3 K8-smoothed values, six lanes take the face neighbours' normals and
 // lane 0 the central differences.  The sums run in the order of smooth_at,
-// parker_youngs and k_fd, so the values are those of the per-cell path; a
+// parker_youngs and fd_cell, so the values are those of the per-cell path; a
 // cell with an obstacle in its 7^3 block (reflected fill levels and wetting
 // normals) takes that path (fd_normal) on lane 0.
 constexpr int FD_WARPS = 4;
 
 // the per-cell path (walls in reach), out of line so that its registers do not
-// weigh on the staged path
+// weigh on the staged path; its helpers (smooth_at, smooth_ext, fd_normal) are
+// out of line too, one copy each instead of an inlined tree of stencils
 __device__ __noinline__ float fd_cell(const Dev &d, int x, int y, int z) {
     float np[3], nm[3], div = 0.f;
     fd_normal(d, x + 1, y, z, np);

@@ -23,6 +23,9 @@ constexpr int MB_BF = 32896;  // bf16 elements of W1 | W2 | w3
 constexpr size_t MB_BIAS = (size_t)MB_BF * 2;  // byte offset of the FP32 biases (256-aligned)
 // FP32 master / gradient / moment layout
 constexpr int M_W1 = 0, M_W2 = 16384, M_W3 = 32768, M_B1 = 32896, M_B2 = 33024, M_B3 = 33152, M_COUNT = 33153;
+static_assert(M_W1 == 0 && M_W2 == M_W1 + MK * MK && M_W3 == M_W2 + MK * MK && M_B1 == MB_BF && M_B2 == M_B1 + MK &&
+                  M_B3 == M_B2 + MK && M_COUNT == M_B3 + 1,
+              "master layout: W1, W2, w3, b1, b2, b3 (the tile partials use the same order)");
 constexpr int MLP_WARPS = 4, MLP_ROWS = 16 * MLP_WARPS;
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
