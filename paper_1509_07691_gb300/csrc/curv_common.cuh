@@ -481,6 +481,40 @@ struct GridAcc {
     }
 };
 
+// Accessor of the general-path kernels: the same values staged in shared
+// memory by one warp per cell (stage_block): the flags of the 5x5x5 block
+// (contact points look one cell past the 3x3x3 block) and the stored normals
+// of the 3x3x3 block.
+struct StagedAcc {
+    const Dev &d;
+    const uint8_t *fl;  // slot ((dz+2)*5 + dy+2)*5 + dx+2
+    const float4 *nm;   // slot (dz+1)*9 + (dy+1)*3 + dx+1
+    __device__ __forceinline__ uint8_t flag(int dx, int dy, int dz) const {
+        return fl[((dz + 2) * 5 + (dy + 2)) * 5 + (dx + 2)];
+    }
+    template <typename T>
+    __device__ __forceinline__ bool normal(int dx, int dy, int dz, T n[3], T &a) const {
+        const float4 q4 = nm[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+        if (q4.x == 0.f && q4.y == 0.f && q4.z == 0.f) return false;
+        n[0] = T(q4.x);
+        n[1] = T(q4.y);
+        n[2] = T(q4.z);
+        a = T(q4.w);
+        return true;
+    }
+    template <typename T>
+    __device__ __forceinline__ void theta(T &ct, T &st) const {
+        ct = T(d.cos_theta_d);
+        st = T(d.sin_theta_d);
+    }
+};
+
+// the lanes of a warp stage the block of cell (x, y, z) for StagedAcc
+__device__ __forceinline__ void stage_block(const Dev &d, int x, int y, int z, int lane, uint8_t *fl, float4 *nm) {
+    for (int e = lane; e < 125; e += 32) fl[e] = d.flags[nbr_index(d, x, y, z, e % 5 - 2, (e / 5) % 5 - 2, e / 25 - 2)];
+    if (lane < 27) nm[lane] = d.normal[nbr_index(d, x, y, z, lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1)];
+}
+
 // Fast path: FP32 normal equations of the full model for an interface cell
 // with no contact-line cell in its neighbourhood.  The 5x5 Gram matrix
 // A^T A and A^T f are accumulated row by row (independent FMAs), then solved

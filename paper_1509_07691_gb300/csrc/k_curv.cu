@@ -61,23 +61,32 @@ __global__ void __launch_bounds__(LIST_THREADS) k_lsqr_fast(Dev d, float *kappa_
 // General path: contact rows and centre constraint, isotropic fallback, FP64
 // re-solve when the FP32 R is ill conditioned
 __global__ void __launch_bounds__(LIST_THREADS) k_lsqr_slow(Dev d, float *kappa_out) {
+    __shared__ uint8_t sfl[LIST_THREADS / 32][128];
+    __shared__ float4 snm[LIST_THREADS / 32][27];
     int cnt[1];
     block_counts<1>(d.counts, {C_SLOW}, cnt);
     const int n = cnt[0];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int k = gw; k < n; k += nw) {  // warp per cell: the block staged, one lane fits
         const int i = d.slow[k];
         int x, y, z;
         cell_coords(d, i, x, y, z);
-        const GridAcc acc{d, x, y, z};
-        const uint8_t fi = d.flags[i];
-        float cond;
-        float kap = lsqr_core<float>(acc, fi, cond);
-        if (cond * cond > d.fp64_cond) {
-            double c2;
-            kap = (float)lsqr_core<double>(acc, fi, c2);
-            atomicAdd(d.counts + C_FP64, 1);
+        stage_block(d, x, y, z, lane, sfl[w], snm[w]);
+        __syncwarp();
+        if (lane == 0) {
+            const StagedAcc acc{d, sfl[w], snm[w]};
+            const uint8_t fi = d.flags[i];
+            float cond;
+            float kap = lsqr_core<float>(acc, fi, cond);
+            if (cond * cond > d.fp64_cond) {
+                double c2;
+                kap = (float)lsqr_core<double>(acc, fi, c2);
+                atomicAdd(d.counts + C_FP64, 1);
+            }
+            kappa_out[i] = kap;
         }
-        kappa_out[i] = kap;
+        __syncwarp();
     }
 }
 
@@ -340,7 +349,7 @@ void launch_normals(const Dev &d, cudaStream_t s) {
 }
 void launch_lsqr(const Dev &d, float *kappa_out, cudaStream_t s) {
     static const int gf = list_blocks((const void *)k_lsqr_fast, LIST_THREADS, 4);
-    static const int gs = list_blocks((const void *)k_lsqr_slow, LIST_THREADS, 1);
+    static const int gs = list_blocks((const void *)k_lsqr_slow, LIST_THREADS, 4);
     k_lsqr_fast<<<gf, LIST_THREADS, 0, s>>>(d, kappa_out);
     k_lsqr_slow<<<gs, LIST_THREADS, 0, s>>>(d, kappa_out);
 }

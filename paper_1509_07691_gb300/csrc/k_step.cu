@@ -8,50 +8,12 @@
 // by k_curv_iface_fast (LSQR model, fit and stream-collide fused) or
 // k_sc_iface (other models) over the interface list; everything after the
 // collision only touches list entries, so no pass sweeps the whole grid.
+#include "collide.cuh"
 #include "curv_common.cuh"
 
 namespace fslk {
 
 constexpr int LIST_BLOCK = 128;
-
-// BGK / TRT collision in place (Eq. lbe2).  TRT relaxes the even and odd
-// parts of each pair (q, opp q) with omega_e = 1/tau and omega_o = 1/tau_o.
-template <int COLL>
-__device__ __forceinline__ void collide(float f[Q], const Dev &d, float &rho_out) {
-    float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        rho += f[q];
-        jx += cx(q) * f[q];
-        jy += cy(q) * f[q];
-        jz += cz(q) * f[q];
-    }
-    const float inv = 1.0f / rho;
-    const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
-    const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
-    rho_out = rho;
-    if (COLL == FSL_BGK) {
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-            const float fe = wq(q) * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - uu);
-            f[q] += d.omega_e * (fe - f[q]);
-        }
-    } else {
-        f[0] += d.omega_e * (wq(0) * rho * (1.0f - uu) - f[0]);
-#pragma unroll
-        for (int q = 1; q < Q; q += 2) {
-            const int qb = q + 1;
-            const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-            const float ep = wq(q) * rho * (1.0f + 4.5f * cu * cu - uu);
-            const float em = wq(q) * rho * 3.0f * cu;
-            const float fp = 0.5f * (f[q] + f[qb]), fm = 0.5f * (f[q] - f[qb]);
-            const float de = d.omega_e * (fp - ep), dd = d.omega_o * (fm - em);
-            f[q] = f[q] - de - dd;
-            f[qb] = f[qb] - de + dd;
-        }
-    }
-}
 
 // index of the source cell x - c_q of every direction
 __device__ __forceinline__ void sources(const Dev &d, int x, int y, int z, int src[Q]) {
@@ -489,27 +451,40 @@ __global__ void __launch_bounds__(LIST_BLOCK, IFACE_MIN_BLOCKS) k_curv_iface_fas
     }
 }
 
+// General-path cells (contact-line cells, degenerate or ill-conditioned FP32
+// fits): one warp per cell stages the block in shared memory, then one lane
+// runs the streaming Givens fit (FP64 when ill conditioned) and the
+// interface stream-collide of the cell.
 template <int S, int COLL>
 __global__ void __launch_bounds__(LIST_BLOCK) k_curv_iface_slow(Dev d) {
     pdl_enter();
+    __shared__ uint8_t sfl[LIST_BLOCK / 32][128];
+    __shared__ float4 snm[LIST_BLOCK / 32][27];
     int cnt[1];
     block_counts<1>(d.counts, {C_SLOW}, cnt);
     const int n = cnt[0];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int k = gw; k < n; k += nw) {
         const int i = d.slow[k];
         int x, y, z;
         cell_coords(d, i, x, y, z);
-        const GridAcc acc{d, x, y, z};
-        const uint8_t fi = d.flags[i] & (T_MASK | B_NEAR);
-        float cond;
-        float kap = lsqr_core<float>(acc, fi, cond);
-        if (cond * cond > d.fp64_cond) {
-            double c2;
-            kap = (float)lsqr_core<double>(acc, fi, c2);
-            atomicAdd(d.counts + C_FP64, 1);
+        stage_block(d, x, y, z, lane, sfl[w], snm[w]);
+        __syncwarp();
+        if (lane == 0) {
+            const StagedAcc acc{d, sfl[w], snm[w]};
+            const uint8_t fi = d.flags[i] & (T_MASK | B_NEAR);
+            float cond;
+            float kap = lsqr_core<float>(acc, fi, cond);
+            if (cond * cond > d.fp64_cond) {
+                double c2;
+                kap = (float)lsqr_core<double>(acc, fi, c2);
+                atomicAdd(d.counts + C_FP64, 1);
+            }
+            d.kappa[i] = kap;
+            iface_cell<S, COLL>(d, i);
         }
-        d.kappa[i] = kap;
-        iface_cell<S, COLL>(d, i);
+        __syncwarp();
     }
 }
 
@@ -825,7 +800,7 @@ void launch_iface(const Dev &d, cudaStream_t s) {
 template <int S, int COLL>
 void launch_ci(const Dev &d, cudaStream_t s) {
     static const int gf = list_blocks((const void *)k_curv_iface_fast<S, COLL, FSL_IFACE_LANES>, LIST_BLOCK, 4);
-    static const int gs = list_blocks((const void *)k_curv_iface_slow<S, COLL>, LIST_BLOCK, 1);
+    static const int gs = list_blocks((const void *)k_curv_iface_slow<S, COLL>, LIST_BLOCK, 4);
     launch_pdl(k_curv_iface_fast<S, COLL, FSL_IFACE_LANES>, gf, LIST_BLOCK, s, d);
     launch_pdl(k_curv_iface_slow<S, COLL>, gs, LIST_BLOCK, s, d);
 }
