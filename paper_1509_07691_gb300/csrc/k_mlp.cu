@@ -254,6 +254,25 @@ __device__ __forceinline__ int canon_index(const Canon &c, int e) {
         if (c.flip[k]) r[k] = 4 - r[k];
     return r[c.order[0]] * 25 + r[c.order[1]] * 5 + r[c.order[2]];
 }
+// The same map as an affine function of the raw coordinates (r0, r1, r2) =
+// (e / 25, e / 5 % 5, e % 5): canonical = base + r0 s0 + r1 s1 + r2 s2, with
+// s_k = +-(the weight 25, 5 or 1 of the place axis k takes) and the flips
+// folded into base.  Per stencil the four numbers, per element three
+// multiply-adds.
+struct CanonAffine {
+    int base, s[3];
+};
+__device__ __forceinline__ CanonAffine canon_affine(const Canon &c) {
+    CanonAffine a;
+    a.base = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int w = c.order[0] == k ? 25 : (c.order[1] == k ? 5 : 1);
+        a.s[k] = c.flip[k] ? -w : w;
+        a.base += c.flip[k] ? 4 * w : 0;
+    }
+    return a;
+}
 
 // mean curvature at the point of the ellipsoid sum (y/a)^2 = 1 (body frame)
 // nearest to o (body frame): x_k = a_k^2 o_k / (a_k^2 + t), bisection on t
@@ -365,7 +384,7 @@ __global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp_curv(Dev d, float *kappa
     MlpSmem &s = *reinterpret_cast<MlpSmem *>(smem_raw);
     __nv_bfloat16 *Xs = reinterpret_cast<__nv_bfloat16 *>(smem_raw + sizeof(MlpSmem));
     float *raw = reinterpret_cast<float *>(Xs + MLP_ROWS * WPAD);  // [MLP_ROWS][128]
-    __shared__ Canon cw[MLP_ROWS];
+    __shared__ CanonAffine cw[MLP_ROWS];
     __shared__ int wall[MLP_ROWS];
     int cnt[1];
     block_counts<1>(d.counts, {d.cif}, cnt);
@@ -402,13 +421,18 @@ __global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp_curv(Dev d, float *kappa
         obsm = __reduce_or_sync(0xffffffffu, obsm);
         if (lane < 16) wall[warp * 16 + lane] = (obsm >> lane) & 1u;
         __syncwarp();
-        if (lane < 16) cw[warp * 16 + lane] = canon_of(rw + lane * MK);
+        if (lane < 16) cw[warp * 16 + lane] = canon_affine(canon_of(rw + lane * MK));
         __syncwarp();
         for (int r = 0; r < 16; ++r) {
-            const Canon c = cw[warp * 16 + r];
-            for (int e = lane; e < MK; e += 32) {
-                if (e < 125) Xw[r * WPAD + canon_index(c, e)] = __float2bfloat16_rn(2.0f * rw[r * MK + e] - 1.0f);
-                else Xw[r * WPAD + e] = __float2bfloat16_rn(0.f);
+            const CanonAffine c = cw[warp * 16 + r];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int e = lane + 32 * t;
+                if (e < 125)
+                    Xw[r * WPAD + c.base + (e / 25) * c.s[0] + ((e / 5) % 5) * c.s[1] + (e % 5) * c.s[2]] =
+                        __float2bfloat16_rn(2.0f * rw[r * MK + e] - 1.0f);
+                else
+                    Xw[r * WPAD + e] = __float2bfloat16_rn(0.f);
             }
         }
         __syncwarp();
