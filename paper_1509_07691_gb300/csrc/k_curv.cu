@@ -17,6 +17,12 @@ namespace fslk {
 
 constexpr int LIST_THREADS = 128;
 
+// Parker-Youngs normal of a cell next to an obstacle (reflected fill levels at
+// the obstacle cells); out of line, so that the loop of k_normals stays short
+__device__ __noinline__ void normal_near_wall(const Dev &d, int x, int y, int z, float nv[3]) {
+    parker_youngs<float>([&](int dx, int dy, int dz) { return phi_ext(d, x + dx, y + dy, z + dz); }, nv);
+}
+
 // The first kernel of a step also runs the step prologue (counters, bubble
 // pressure); every later kernel of the step is ordered after it on the stream.
 __global__ void __launch_bounds__(LIST_THREADS) k_normals(Dev d) {
@@ -31,7 +37,7 @@ __global__ void __launch_bounds__(LIST_THREADS) k_normals(Dev d) {
         cell_coords(d, i, x, y, z);
         float nv[3], a;
         if (d.flags[i] & B_NEAR)
-            parker_youngs<float>([&](int dx, int dy, int dz) { return phi_ext(d, x + dx, y + dy, z + dz); }, nv);
+            normal_near_wall(d, x, y, z, nv);
         else
             parker_youngs<float>([&](int dx, int dy, int dz) { return d.phi[nbr_index(d, x, y, z, dx, dy, dz)]; }, nv);
         const bool ok = unit_normal_offset<float>(nv, d.phi[i], d.plic_iters, a);

@@ -651,6 +651,25 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
 //    and the new ones) set phi = m / rho and form the interface list of t+1;
 //    those k_convert marked as receivers first gather the excess mass of their
 //    converted neighbours in fixed q order (and clear the mark).
+// excess mass of the converted neighbours of receiver i added to its mass m
+// (out of line: few cells per step take it, and the list loop stays short)
+__device__ __noinline__ float gather_excess(const Dev &d, int i, float m) {
+    d.rmark[i] = 0;
+    int x, y, z;
+    cell_coords(d, i, x, y, z);
+    for (int q = 1; q < Q; ++q) {
+        const int j = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
+        const uint8_t fj = d.flags[j];
+        if (!(fj & (B_TOLIQ | B_TOGAS))) continue;
+        // the share of this cell, at -c_q seen from the converted cell j
+        const float w =
+            d.exw[j] != 0.f ? excess_weight(d.normal[j], (fj & B_TOLIQ) != 0, -cx(q), -cy(q), -cz(q)) : 1.f;
+        m += d.excess[j] * w;
+    }
+    d.mass[i] = m;
+    return m;
+}
+
 __global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
     pdl_enter();
     int cnt[6];
@@ -667,22 +686,7 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
             const uint8_t fl = d.flags[i];
             if (!(k < nold && (fl & (B_TOLIQ | B_TOGAS)))) {
                 float m = d.mass[i];
-                if (any && d.rmark[i]) {  // a converted neighbour shares its excess with this cell
-                    d.rmark[i] = 0;
-                    int x, y, z;
-                    cell_coords(d, i, x, y, z);
-                    for (int q = 1; q < Q; ++q) {
-                        const int j = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
-                        const uint8_t fj = d.flags[j];
-                        if (!(fj & (B_TOLIQ | B_TOGAS))) continue;
-                        // the share of this cell, at -c_q seen from the converted cell j
-                        const float w = d.exw[j] != 0.f
-                                            ? excess_weight(d.normal[j], (fj & B_TOLIQ) != 0, -cx(q), -cy(q), -cz(q))
-                                            : 1.f;
-                        m += d.excess[j] * w;
-                    }
-                    d.mass[i] = m;
-                }
+                if (any && d.rmark[i]) m = gather_excess(d, i, m);  // a converted neighbour shares its excess
                 const float ph = m / d.rho[i];
                 d.phi[i] = ph;
                 if (d.bub_i) phisum += __double2ll_rn((double)ph * BUB_FIX);
