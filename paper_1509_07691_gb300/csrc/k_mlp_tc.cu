@@ -1,7 +1,9 @@
-// k_mlp_tc.cu -- forward pass of the learned-curvature MLP (125 -> 128 -> 128
-// -> 1, GELU, BF16 weights, FP32 accumulate; see k_mlp.cu) over a batch of
-// stencils on the 5th-generation tensor cores: tcgen05.mma with both operands
-// in shared memory and the FP32 accumulators in tensor memory (TMEM).
+// k_mlp_tc.cu -- the learned-curvature MLP (125 -> 128 -> 128 -> 1, GELU,
+// BF16 weights, FP32 accumulate; see k_mlp.cu) on the 5th-generation tensor
+// cores: tcgen05.mma with both operands in shared memory and the FP32
+// accumulators in tensor memory (TMEM).  Three kernels: the forward pass over
+// a batch of stencils (below), the training step of a 128-row tile, and the
+// in-step estimate over the interface list.
 //
 // One CTA (8 warps) per 128-row tile of the batch, persistent over tiles:
 //   layer 1  D1[128 x 128] = X[128 x 128] W1^T   (8 MMAs, M = N = 128, K = 16)
@@ -18,6 +20,7 @@
 #include <math.h>
 
 #include "fsl_internal.cuh"
+#include "mlp_common.cuh"
 
 namespace fslk {
 
@@ -133,8 +136,8 @@ __device__ __forceinline__ void load_tile(char *tile, const __nv_bfloat16 *src, 
 }  // namespace
 
 // Descriptors: leading byte offset = stride between core matrices along K,
-// stride byte offset = stride between 8-row groups (checked against the
-// mma.sync network: identical pre-activations).
+// stride byte offset = stride between 8-row groups (the outputs are checked
+// against the FP64 oracle network in the tests).
 template <bool STORE>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_forward_tc(const uint8_t *params, const __nv_bfloat16 *X, int n,
                                                                   float *y, float *z1, float *z2, int *status) {
@@ -251,6 +254,201 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_forward_tc(const uint8_t 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// ---- the learned curvature inside the step, on the tensor cores -----------------
+// One CTA (16 warps) per SM, persistent over 128-cell tiles of the interface
+// list.  Warp w takes rows 8w .. 8w+7 of a tile: lane r < 8 finds cell r's
+// canonical order from its 3x3x3 fill levels, then the warp gathers the 5x5x5
+// fill levels of four cells at a time straight into the canonical BF16 rows
+// of X (x = 2 phi - 1).  The two layers run as in k_mlp_forward_tc (MMAs into
+// TMEM, GELU epilogues; thread (row, column quarter) reads 32 accumulator
+// columns), the four quarters' parts of y are summed in order, and the LSQR
+// value already in kappa_out judges: the network's value is kept where
+// |y - k_lsqr| <= rel |k_lsqr| and no obstacle cell lies in the stencil.
+constexpr int CV_THREADS = 512;
+
+struct CvSmem {
+    __nv_bfloat16 W1[TILE * TILE];
+    __nv_bfloat16 W2[TILE * TILE];
+    __nv_bfloat16 X[TILE * TILE];
+    __nv_bfloat16 H[TILE * TILE];
+    float b1[TILE], b2[TILE], w3[TILE];
+    float ypart[4][TILE];
+    int cell[TILE];  // interface cell of each row, -1 past the end of the list
+    int wall[TILE];  // 1: an obstacle cell in the row's stencil
+    float b3;
+    uint32_t tmem_base;
+    unsigned long long mbar;
+};
+
+__global__ void __launch_bounds__(CV_THREADS, 1) k_mlp_curv_tc(Dev d, float *kappa_out, int *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    CvSmem &s = *reinterpret_cast<CvSmem *>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int cnt[1];
+    block_counts<1>(d.counts, {d.cif}, cnt);
+    const int n = cnt[0];
+    const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(d.mlp_params);
+    const float *bias = reinterpret_cast<const float *>(d.mlp_params + MB_BIAS_TC);
+    load_tile(reinterpret_cast<char *>(s.W1), wb, TILE, TILE);
+    load_tile(reinterpret_cast<char *>(s.W2), wb + TILE * TILE, TILE, TILE);
+    for (int e = threadIdx.x; e < TILE; e += blockDim.x) {
+        s.b1[e] = bias[e];
+        s.b2[e] = bias[TILE + e];
+        s.w3[e] = __bfloat162float(wb[2 * TILE * TILE + e]);
+    }
+    if (threadIdx.x == 0) {
+        s.b3 = bias[2 * TILE];
+        mbar_init(&s.mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s.tmem_base;
+    const int q4 = warp & 3, cq = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(32 * q4) << 16;  // this warp's TMEM lanes
+    const int row = 32 * q4 + lane;                         // tile row of this thread in the epilogues
+    const int col0 = 32 * cq;                               // its 32 accumulator columns
+    const uint32_t aX = smem_u32(s.X), aH = smem_u32(s.H), aW1 = smem_u32(s.W1), aW2 = smem_u32(s.W2);
+    char *Xb = reinterpret_cast<char *>(s.X);
+    uint32_t phase = 0;
+    int evaluated = 0, kept = 0;
+    for (long long t0 = (long long)blockIdx.x * TILE; t0 < n; t0 += (long long)gridDim.x * TILE) {
+        // ---- gather: rows r0 .. r0 + 7 of this warp
+        const int r0 = warp * 8;
+        int cx0 = 0, cy0 = 0, cz0 = 0, ci = -1;
+        CanonAffine ca{0, {0, 0, 0}};
+        if (lane < 8 && t0 + r0 + lane < n) {
+            ci = d.iflist[t0 + r0 + lane];
+            cell_coords(d, ci, cx0, cy0, cz0);
+            ca = canon_affine(
+                canon_at([&](int dx, int dy, int dz) { return d.phi[nbr_index(d, cx0, cy0, cz0, dx, dy, dz)]; }));
+        }
+        if (lane < 8) s.cell[r0 + lane] = ci;
+        unsigned obsm = 0u;
+#pragma unroll 4
+        for (int r = 0; r < 8; ++r) {
+            const int x = __shfl_sync(0xffffffffu, cx0, r), y = __shfl_sync(0xffffffffu, cy0, r),
+                      z = __shfl_sync(0xffffffffu, cz0, r);
+            const int cb = __shfl_sync(0xffffffffu, ca.base, r), s0 = __shfl_sync(0xffffffffu, ca.s[0], r),
+                      s1 = __shfl_sync(0xffffffffu, ca.s[1], r), s2 = __shfl_sync(0xffffffffu, ca.s[2], r);
+            const bool rv = t0 + r0 + r < n;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int e = lane + 32 * t;
+                if (e < 125) {
+                    float v = 0.f;
+                    if (rv) {
+                        const int j = nbr_index(d, x, y, z, e / 25 - 2, (e / 5) % 5 - 2, e % 5 - 2);
+                        v = d.phi[j];
+                        obsm |= (d.flags[j] & T_OBS) ? (1u << r) : 0u;
+                    }
+                    const int k = cb + (e / 25) * s0 + ((e / 5) % 5) * s1 + (e % 5) * s2;
+                    *reinterpret_cast<__nv_bfloat16 *>(Xb + tile_off(r0 + r, k)) = __float2bfloat16_rn(2.0f * v - 1.0f);
+                } else {
+                    *reinterpret_cast<__nv_bfloat16 *>(Xb + tile_off(r0 + r, e)) = __float2bfloat16_rn(0.f);
+                }
+            }
+        }
+        obsm = __reduce_or_sync(0xffffffffu, obsm);
+        if (lane < 8) s.wall[r0 + lane] = (obsm >> lane) & 1u;
+        proxy_fence();
+        __syncthreads();
+        // ---- layer 1
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < TILE / 16; ++kk)
+                tc_mma(tmem, smem_desc(aX + kk * 2 * CORE_K, CORE_K, CORE_MN),
+                       smem_desc(aW1 + kk * 2 * CORE_K, CORE_K, CORE_MN), kk > 0);
+            tc_commit(&s.mbar);
+        }
+        if (__syncthreads_or(mbar_wait(&s.mbar, phase) ? 0 : 1)) {
+            if (threadIdx.x == 0) set_status(status, FSL_ETIMEOUT);
+            break;
+        }
+        phase ^= 1;
+        tc_fence_after();
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = col0 + 16 * cc;
+            float v[16];
+            tc_ld16(tmem + lane_base + c, v);
+            uint32_t h[8];
+#pragma unroll
+            for (int e = 0; e < 16; e += 2)
+                h[e >> 1] = pack2(gelu_tc(v[e] + s.b1[c + e]), gelu_tc(v[e + 1] + s.b1[c + e + 1]));
+            char *Hb = reinterpret_cast<char *>(s.H);
+            *reinterpret_cast<uint4 *>(Hb + tile_off(row, c)) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(Hb + tile_off(row, c + 8)) = make_uint4(h[4], h[5], h[6], h[7]);
+        }
+        tc_fence_before();
+        proxy_fence();
+        __syncthreads();
+        // ---- layer 2
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < TILE / 16; ++kk)
+                tc_mma(tmem + TILE, smem_desc(aH + kk * 2 * CORE_K, CORE_K, CORE_MN),
+                       smem_desc(aW2 + kk * 2 * CORE_K, CORE_K, CORE_MN), kk > 0);
+            tc_commit(&s.mbar);
+        }
+        if (__syncthreads_or(mbar_wait(&s.mbar, phase) ? 0 : 1)) {
+            if (threadIdx.x == 0) set_status(status, FSL_ETIMEOUT);
+            break;
+        }
+        phase ^= 1;
+        tc_fence_after();
+        float yp = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = col0 + 16 * cc;
+            float v[16];
+            tc_ld16(tmem + TILE + lane_base + c, v);
+#pragma unroll
+            for (int e = 0; e < 16; e += 2)
+                yp += gelu_tc(v[e] + s.b2[c + e]) * s.w3[c + e] + gelu_tc(v[e + 1] + s.b2[c + e + 1]) * s.w3[c + e + 1];
+        }
+        s.ypart[cq][row] = yp;
+        tc_fence_before();
+        __syncthreads();
+        // ---- the judge
+        if (cq == 0) {
+            const int i = s.cell[row];
+            if (i >= 0 && !s.wall[row]) {
+                const float y = ((s.ypart[0][row] + s.ypart[1][row]) + s.ypart[2][row]) + s.ypart[3][row] + s.b3;
+                const float kls = kappa_out[i];
+                ++evaluated;
+                if (fabsf(y - kls) <= d.mlp_rel * fabsf(kls)) {
+                    kappa_out[i] = y;
+                    ++kept;
+                }
+            }
+        }
+        __syncthreads();  // X, H, the row tables and ypart are rewritten by the next tile
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        evaluated += __shfl_xor_sync(0xffffffffu, evaluated, o);
+        kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    }
+    if (lane == 0 && evaluated) {
+        atomicAdd(d.counts + C_MLP, evaluated);
+        atomicAdd(d.counts + C_MLPKEEP, kept);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
 // derivative of the GELU (erf form)
 __device__ __forceinline__ float gelu_grad_tc(float x) {
     return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
@@ -619,6 +817,23 @@ int launch_mlp_train_tile(const uint8_t *params, const __nv_bfloat16 *X, const f
         return FSL_ECUDA;
     k_mlp_train_tile<<<(n + TILE - 1) / TILE, FT_THREADS, sm, s>>>(params, X, target, perm, row0, n, n_all, part, lpart,
                                                                    st);
+    return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
+}
+
+// the learned curvature of the step's interface cells on the tensor cores: one
+// CTA per SM (about 135 KB of shared memory, 256 TMEM columns), persistent
+// over the 128-cell tiles of the list (its length is read on the device)
+int launch_mlp_curv_tc(const Dev &d, float *kappa_out, cudaStream_t s) {
+    int *st = status_ptr();
+    if (!st) return FSL_ECUDA;
+    const size_t sm = sizeof(CvSmem) + 1024;
+    static const bool attr =
+        cudaFuncSetAttribute(k_mlp_curv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) == cudaSuccess;
+    if (!attr) return FSL_ECUDA;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_mlp_curv_tc<<<sms > 0 ? sms : 1, CV_THREADS, sm, s>>>(d, kappa_out, st);
     return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
 }
 
