@@ -501,10 +501,19 @@ def learned_curvature(F, S, stream, flush, peaks, seed, n_train, epochs, steps, 
         b.record(stream)
     torch.cuda.synchronize()
     cm = sum(a.elapsed_time(b) for a, b in cev) / len(cev)
+    for a, b in cev:  # the LSQR part alone on the same state: the network's share is the difference
+        flush.fill_(1.0)
+        a.record(stream)
+        sim.curvature(F.CURV_LSQR, kap)
+        b.record(stream)
+    torch.cuda.synchronize()
+    cl = sum(a.elapsed_time(b) for a, b in cev) / len(cev)
     out["inference"] = {"workload": "coalescence384", "grid": list(w["shape"][::-1]), "fluid_cells": n_fluid,
                         "interface_cells": n_if, "mlups": n_fluid * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
                         "mlp_cells_last_step": int(st[8]), "kept_fraction": float(st[9]) / max(1, int(st[8])),
-                        "curvature_ms_lsqr_plus_mlp": cm, "curvature_evals_per_s": n_if / (cm * 1e-3)}
+                        "curvature_ms_lsqr_plus_mlp": cm, "curvature_ms_lsqr": cl,
+                        "network_ms": cm - cl, "network_flops_per_s": n_if * 2 * (125 * 128 + 128 * 128 + 128) / ((cm - cl) * 1e-3),
+                        "curvature_evals_per_s": n_if / (cm * 1e-3)}
     sim.close()
     del sim, phi0
     torch.cuda.empty_cache()

@@ -742,9 +742,45 @@ __global__ void __launch_bounds__(256) k_fin_b(Dev d) {
         }
     }
     if (!cnt[4]) return;  // the set of active segments did not change (block-uniform)
-    for (int base = blockIdx.x * blockDim.x; base < d.nseg; base += nth) {
-        const int s = base + threadIdx.x;
-        block_append(d.seg_list, d.counts + C_SEG, s < d.nseg && d.seg_active[s], s);
+    // the list again: 16 segment flags per thread (one 16-byte load), a warp
+    // scan of the counts and one atomic per warp for the warp's place
+    const int lane = threadIdx.x & 31, nchunk = (d.nseg + 15) >> 4;
+    for (int base = tid - lane; base < nchunk; base += nth) {  // warp-uniform
+        const int c = base + lane;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (c < nchunk) {
+            if (16 * c + 16 <= d.nseg) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(d.seg_active + 16 * c);
+                w[0] = v.x;
+                w[1] = v.y;
+                w[2] = v.z;
+                w[3] = v.w;
+            } else {
+                for (int b = 0; 16 * c + b < d.nseg; ++b)
+                    w[b >> 2] |= (uint32_t)(d.seg_active[16 * c + b] != 0) << (8 * (b & 3));
+            }
+        }
+        uint32_t m = 0u;  // bit b: segment 16 c + b is active
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) m |= (((w[k] >> (8 * b)) & 0xffu) != 0u ? 1u : 0u) << (4 * k + b);
+        const int cntl = __popc(m);
+        int incl = cntl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int wbase = 0;
+        if (lane == 31 && incl) wbase = atomicAdd(d.counts + C_SEG, incl);
+        wbase = __shfl_sync(0xffffffffu, wbase, 31);
+        int pos = wbase + incl - cntl;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            d.seg_list[pos++] = 16 * c + b;
+        }
     }
 }
 
