@@ -526,30 +526,32 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
     }
     __syncthreads();
     // B
+    // (the cell's type, the neighbours' types and segment flags are loaded
+    // together, before the cell's type decides whether the warp goes on)
     for (int k = warp; k < nfill + nempty; k += nwarps) {
         const bool isfill = k < nfill;
         const int i = isfill ? d.fill[k] : d.empty[k - nfill];
-        if (!isfill && !(__ldcg(d.flags + i) & B_TOGAS)) continue;  // warp-uniform
         int x, y, z;
         cell_coords(d, i, x, y, z);
-        if (act) {
-            const int j = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
-            const uint8_t fj = __ldcg(d.flags + j);
-            if (isfill ? (fj & T_GAS) : (fj & T_LIQ)) {
-                unsigned *word = reinterpret_cast<unsigned *>(d.flags + (j & ~3));
-                const int sh = (j & 3) * 8;
-                const unsigned old = atomicOr(word, (unsigned)B_NEW << sh);
-                if (!((old >> sh) & B_NEW)) {
-                    if (isfill) {
-                        d.newgas[atomicAdd(d.counts + C_NEWGAS, 1)] = j;
-                        const int sj = seg_of(d, j);
-                        if (!d.seg_active[sj]) {
-                            d.seg_active[sj] = 1;
-                            d.counts[d.cdirty] = 1;
-                        }
-                    } else {
-                        d.liq2if[atomicAdd(d.counts + C_LIQ2IF, 1)] = j;
+        const int j = act ? nbr_index(d, x, y, z, cx(q), cy(q), cz(q)) : i;
+        const uint8_t fi = isfill ? (uint8_t)0 : __ldcg(d.flags + i);
+        const uint8_t fj = act ? __ldcg(d.flags + j) : (uint8_t)0;
+        const int sj = seg_of(d, j);
+        const uint8_t sa = (act && isfill) ? d.seg_active[sj] : (uint8_t)1;
+        if (!isfill && !(fi & B_TOGAS)) continue;  // warp-uniform
+        if (act && (isfill ? (fj & T_GAS) : (fj & T_LIQ))) {
+            unsigned *word = reinterpret_cast<unsigned *>(d.flags + (j & ~3));
+            const int sh = (j & 3) * 8;
+            const unsigned old = atomicOr(word, (unsigned)B_NEW << sh);
+            if (!((old >> sh) & B_NEW)) {
+                if (isfill) {
+                    d.newgas[atomicAdd(d.counts + C_NEWGAS, 1)] = j;
+                    if (!sa) {
+                        d.seg_active[sj] = 1;
+                        d.counts[d.cdirty] = 1;
                     }
+                } else {
+                    d.liq2if[atomicAdd(d.counts + C_LIQ2IF, 1)] = j;
                 }
             }
         }
@@ -564,17 +566,19 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
             const int kc = k - ngas - nliq;
             const bool isfill = kc < nfill;
             const int i = isfill ? d.fill[kc] : d.empty[kc - nfill];
-            if (!isfill && !(__ldcg(d.flags + i) & B_TOGAS)) continue;  // warp-uniform
             int x, y, z;
             cell_coords(d, i, x, y, z);
+            const int j = act ? nbr_index(d, x, y, z, cx(q), cy(q), cz(q)) : i;
+            const uint8_t fi = isfill ? (uint8_t)0 : __ldcg(d.flags + i);
+            const uint8_t fj = act ? __ldcg(d.flags + j) : (uint8_t)0;
+            const float4 ni = d.excess_rule ? d.normal[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!isfill && !(fi & B_TOGAS)) continue;  // warp-uniform
             bool recv = false;
             float wgt = 0.f;
             if (act) {
-                const int j = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
-                const uint8_t fj = __ldcg(d.flags + j);
                 recv = ((fj & T_IF) && !(fj & (B_TOLIQ | B_TOGAS))) || (fj & B_NEW);
                 if (recv) d.rmark[j] = 1;
-                if (recv && d.excess_rule) wgt = excess_weight(d.normal[i], isfill, cx(q), cy(q), cz(q));
+                if (recv && d.excess_rule) wgt = excess_weight(ni, isfill, cx(q), cy(q), cz(q));
             }
             const int n = __popc(__ballot_sync(0xffffffffu, recv));
             float W = wgt;  // sum of the receivers' weights, fixed order
@@ -596,17 +600,20 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
             int x, y, z;
             cell_coords(d, j, x, y, z);
             float r = 0.f, ux = 0.f, uy = 0.f, uz = 0.f, c = 0.f;
-            if (act) {
+            if (act) {  // the neighbour's PDFs are loaded with its type (used only if it is fluid)
                 const int l = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
-                if (__ldcg(d.flags + l) & (T_LIQ | T_IF)) {
+                const uint8_t fl = __ldcg(d.flags + l);
+                float v[Q];
+#pragma unroll
+                for (int p = 0; p < Q; ++p) v[p] = St::ldcg(d.fdst, (long long)p * N + l, p, d);
+                if (fl & (T_LIQ | T_IF)) {
                     float jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
                     for (int p = 0; p < Q; ++p) {
-                        const float v = St::ldcg(d.fdst, (long long)p * N + l, p, d);
-                        r += v;
-                        jx += cx(p) * v;
-                        jy += cy(p) * v;
-                        jz += cz(p) * v;
+                        r += v[p];
+                        jx += cx(p) * v[p];
+                        jy += cy(p) * v[p];
+                        jz += cz(p) * v[p];
                     }
                     ux = jx / r;
                     uy = jy / r;
@@ -653,14 +660,24 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
 //    converted neighbours in fixed q order (and clear the mark).
 // excess mass of the converted neighbours of receiver i added to its mass m
 // (out of line: few cells per step take it, and the list loop stays short)
+// (the 18 neighbours' types are loaded before any is used: one round of loads,
+// then the converted neighbours' excess in the order of q)
 __device__ __noinline__ float gather_excess(const Dev &d, int i, float m) {
     d.rmark[i] = 0;
     int x, y, z;
     cell_coords(d, i, x, y, z);
+    int js[Q];
+    uint8_t fjs[Q];
+#pragma unroll
     for (int q = 1; q < Q; ++q) {
-        const int j = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
-        const uint8_t fj = d.flags[j];
+        js[q] = nbr_index(d, x, y, z, cx(q), cy(q), cz(q));
+        fjs[q] = d.flags[js[q]];
+    }
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const uint8_t fj = fjs[q];
         if (!(fj & (B_TOLIQ | B_TOGAS))) continue;
+        const int j = js[q];
         // the share of this cell, at -c_q seen from the converted cell j
         const float w =
             d.exw[j] != 0.f ? excess_weight(d.normal[j], (fj & B_TOLIQ) != 0, -cx(q), -cy(q), -cz(q)) : 1.f;
