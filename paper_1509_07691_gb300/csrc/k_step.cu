@@ -516,29 +516,25 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const bool act = lane >= 1 && lane < Q;
     const int q = act ? lane : 1;
-    // A
-    for (int k = warp; k < nempty; k += nwarps) {
-        const int i = d.empty[k];
-        int x, y, z;
-        cell_coords(d, i, x, y, z);
-        const bool tl = act && (d.flags[nbr_index(d, x, y, z, cx(q), cy(q), cz(q))] & B_TOLIQ);
-        if (__any_sync(0xffffffffu, tl) && lane == 0) d.flags[i] &= (uint8_t)~B_TOGAS;
-    }
-    __syncthreads();
-    // B
-    // (the cell's type, the neighbours' types and segment flags are loaded
-    // together, before the cell's type decides whether the warp goes on)
+    // A and B, one pass: a warp takes a converted cell and loads its
+    // neighbours' types and segment flags once.  A needs only the cell's own
+    // neighbours' B_TOLIQ bits (set before this kernel), and B of a cell only
+    // its own A decision and its neighbours' types, so no barrier separates
+    // them; the B_NEW bits B sets on other cells' flag words are atomic, and
+    // A's clearing of the cell's own B_TOGAS touches only its own byte.
     for (int k = warp; k < nfill + nempty; k += nwarps) {
         const bool isfill = k < nfill;
         const int i = isfill ? d.fill[k] : d.empty[k - nfill];
         int x, y, z;
         cell_coords(d, i, x, y, z);
         const int j = act ? nbr_index(d, x, y, z, cx(q), cy(q), cz(q)) : i;
-        const uint8_t fi = isfill ? (uint8_t)0 : __ldcg(d.flags + i);
         const uint8_t fj = act ? __ldcg(d.flags + j) : (uint8_t)0;
         const int sj = seg_of(d, j);
         const uint8_t sa = (act && isfill) ? d.seg_active[sj] : (uint8_t)1;
-        if (!isfill && !(fi & B_TOGAS)) continue;  // warp-uniform
+        if (!isfill && __any_sync(0xffffffffu, act && (fj & B_TOLIQ))) {  // warp-uniform
+            if (lane == 0) d.flags[i] &= (uint8_t)~B_TOGAS;  // A: stays interface
+            continue;
+        }
         if (act && (isfill ? (fj & T_GAS) : (fj & T_LIQ))) {
             unsigned *word = reinterpret_cast<unsigned *>(d.flags + (j & ~3));
             const int sh = (j & 3) * 8;
@@ -572,6 +568,7 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
             const uint8_t fi = isfill ? (uint8_t)0 : __ldcg(d.flags + i);
             const uint8_t fj = act ? __ldcg(d.flags + j) : (uint8_t)0;
             const float4 ni = d.excess_rule ? d.normal[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float m = lane == 0 ? __ldcg(d.mass + i) : 0.f, r = lane == 0 ? __ldcg(d.rho + i) : 0.f;
             if (!isfill && !(fi & B_TOGAS)) continue;  // warp-uniform
             bool recv = false;
             float wgt = 0.f;
@@ -585,7 +582,6 @@ __global__ void __launch_bounds__(CONV_BLOCK) k_convert(Dev d) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
             if (lane == 0) {
-                const float m = __ldcg(d.mass + i), r = __ldcg(d.rho + i);
                 const float mex = isfill ? m - r : m;
                 const bool weighted = d.excess_rule && W > 0.f;
                 d.mass[i] = isfill ? r : 0.f;
@@ -700,11 +696,14 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_fin_a(Dev d) {
         int i = 0;
         if (valid) {
             i = k < nold ? d.iflist[k] : (k < nold + ngas ? d.newgas[k - nold] : d.liq2if[k - nold - ngas]);
+            // the cell's values in one round of loads
             const uint8_t fl = d.flags[i];
+            float m = d.mass[i];
+            const float rh = d.rho[i];
+            const uint8_t rm = any ? d.rmark[i] : (uint8_t)0;
             if (!(k < nold && (fl & (B_TOLIQ | B_TOGAS)))) {
-                float m = d.mass[i];
-                if (any && d.rmark[i]) m = gather_excess(d, i, m);  // a converted neighbour shares its excess
-                const float ph = m / d.rho[i];
+                if (rm) m = gather_excess(d, i, m);  // a converted neighbour shares its excess
+                const float ph = m / rh;
                 d.phi[i] = ph;
                 if (d.bub_i) phisum += __double2ll_rn((double)ph * BUB_FIX);
                 keep = true;
