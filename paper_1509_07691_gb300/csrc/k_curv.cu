@@ -35,12 +35,18 @@ __global__ void __launch_bounds__(LIST_THREADS) k_normals(Dev d) {
         const int i = d.iflist[k];
         int x, y, z;
         cell_coords(d, i, x, y, z);
+        // the 27 fill levels are loaded with the cell's type (one round); a cell
+        // next to a wall takes the reflected ones instead, out of line
+        float ph[27];
+#pragma unroll
+        for (int t = 0; t < 27; ++t) ph[t] = d.phi[nbr_index(d, x, y, z, t % 3 - 1, (t / 3) % 3 - 1, t / 9 - 1)];
+        const uint8_t fl = d.flags[i];
         float nv[3], a;
-        if (d.flags[i] & B_NEAR)
+        if (fl & B_NEAR)
             normal_near_wall(d, x, y, z, nv);
         else
-            parker_youngs<float>([&](int dx, int dy, int dz) { return d.phi[nbr_index(d, x, y, z, dx, dy, dz)]; }, nv);
-        const bool ok = unit_normal_offset<float>(nv, d.phi[i], d.plic_iters, a);
+            parker_youngs<float>([&](int dx, int dy, int dz) { return ph[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)]; }, nv);
+        const bool ok = unit_normal_offset<float>(nv, ph[13], d.plic_iters, a);
         d.normal[i] = ok ? make_float4(nv[0], nv[1], nv[2], a) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
