@@ -376,6 +376,17 @@ def phase_profile(sim, nprof, flush):
     return ph / nprof
 
 
+def launches_per_step(curv, obs):
+    """Kernels of one recorded step: normals, the curvature (LSQR: the fused fit
+    + interface stream-collide, plus the general-path kernel when some cell has
+    an obstacle neighbour; FD / none: curvature, then the interface
+    stream-collide), the liquid stream-collide, conversion and the two final
+    updates."""
+    if curv == "lsqr":
+        return 7 if obs is not None and bool(obs.any()) else 6
+    return 7
+
+
 def measured_traffic(kernel, workload):
     """DRAM bytes per launch from the committed ncu capture (profiles/ncu_traffic.json),
     or None when the kernel's source changed since the capture."""
@@ -1095,7 +1106,7 @@ def run_fsl(args):
             "lsqr_fp64_cells": n_fp64,
             "phases_ms": dict(zip(PHASES, [round(float(v), 5) for v in ph])),
             "mass_reduce_ms": mass_ms, "mass_drift_rel": drift, "roofline": roof, "e2e": e2e,
-            "gpu_launches": {"lsqr": 7, "fd": 7, "none": 7}[args.curv] * args.steps, "clocks": clocks}
+            "gpu_launches": launches_per_step(args.curv, obs) * args.steps, "clocks": clocks}
     gs = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         gs = {"flags": sim2.flags_current().cpu().numpy(), "phi": sim2.phi.double().cpu().numpy()}

@@ -180,6 +180,24 @@ Dev dev_for(const fsl_ctx *c, int parity) {
         if ((call) != cudaSuccess) return FSL_ECUDA; \
     } while (0)
 
+// After the near-obstacle bits were (re)computed: with no cell next to an
+// obstacle no fit has a contact line, and the fused fit + interface kernel
+// finishes the few fits it defers itself (the general-path kernel is not
+// launched).  Recorded graphs of the other kind are dropped.
+int read_near(fsl_ctx *c) {
+    CK(cudaMemcpyAsync(c->host_count, c->base.counts + C_NEAR, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int inl = *c->host_count == 0 ? 1 : 0;
+    if (inl != c->base.inline_general)
+        for (int k = 0; k < 2; ++k)
+            if (c->graph[k]) {
+                cudaGraphExecDestroy(c->graph[k]);
+                c->graph[k] = nullptr;
+            }
+    c->base.inline_general = inl;
+    return FSL_OK;
+}
+
 // enqueue the curvature of the current state into kappa_out
 void enqueue_curvature(const Dev &d, int model, float *kappa_out, cudaStream_t s) {
     launch_normals(d, s);
@@ -193,7 +211,9 @@ void enqueue_curvature(const Dev &d, int model, float *kappa_out, cudaStream_t s
 // One time step from parity p (see fsl_step), recorded as a graph with two
 // branches: the liquid stream-collide does not need the curvature, so it runs
 // beside normals -> LSQR -> interface stream-collide; both join before the
-// conversion.  The counters of the step are zeroed by its first kernel.
+// conversion.  The counters of the step are zeroed by its first kernel.  The
+// kernels after the first of each branch start with a programmatic-launch
+// wait, so each is dispatched while its predecessor drains.
 int enqueue_step_graph(const fsl_ctx *c, int parity) {
     const Dev d = dev_for(c, parity);
     cudaStream_t s = c->cap_stream, side = c->cap_side;
@@ -435,6 +455,7 @@ int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *ph
         const size_t fbytes = (size_t)Q * N * pdf_elem_bytes(c->p.storage);
         if (cudaMemcpyAsync(fields->f[1], fields->f[0], fbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) break;
         if (cudaGetLastError() != cudaSuccess) break;
+        if (read_near(c) != FSL_OK) break;
         c->parity = 0;
         rc = FSL_OK;
     } while (0);
@@ -459,7 +480,8 @@ int fsl_refresh(fsl_ctx *c) {
         CK(cudaMemsetAsync(c->base.bub_i, 0, 5 * sizeof(long long), c->stream));
         launch_bubble_count(d, c->stream);
     }
-    return cudaGetLastError() == cudaSuccess ? FSL_OK : FSL_ECUDA;
+    CK(cudaGetLastError());
+    return read_near(c);
 }
 
 int fsl_step(fsl_ctx *c, int nsteps) {

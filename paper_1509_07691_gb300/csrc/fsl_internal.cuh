@@ -50,7 +50,10 @@ enum : uint8_t {
 // two "segment set changed" flags (one per step parity: a step sets its own,
 // clears the next step's, and rebuilds the segment list only if it is set)
 enum { C_IF0 = 0, C_IF1 = 1, C_FILL = 2, C_EMPTY = 3, C_NEWGAS = 4, C_LIQ2IF = 5, C_FP64 = 6, C_SEG = 7, C_SLOW = 8,
-       C_MLP = 9, C_MLPKEEP = 10, C_ADJ64 = 11, C_SEGD0 = 12, C_SEGD1 = 13, C_ADJGEN = 14, C_NCOUNT = 16 };
+       C_MLP = 9, C_MLPKEEP = 10, C_ADJ64 = 11, C_SEGD0 = 12, C_SEGD1 = 13, C_ADJGEN = 14, C_NEAR = 15,
+       C_NCOUNT = 16 };
+// C_NEAR is 1 when some cell has an obstacle neighbour (set with the
+// near-obstacle bits at initialisation and refresh; no step changes it)
 
 // the grid is walked in x-row segments of SEG cells (one warp each); a
 // segment is active while it holds a liquid or interface cell
@@ -124,6 +127,9 @@ struct Dev {
     float cos_theta, sin_theta;
     float scale, inv_scale;  // 16-bit offset storage
     float fp64_cond;
+    // 1: no cell has an obstacle neighbour, so no fit has a contact line and
+    // the fused fit + interface kernel finishes its few deferred fits itself
+    int inline_general;
     double cos_theta_d, sin_theta_d;
     // learned curvature (FSL_CURV_MLP): packed parameters, judge tolerance
     const uint8_t *mlp_params;

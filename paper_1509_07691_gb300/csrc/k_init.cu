@@ -150,10 +150,10 @@ __global__ void __launch_bounds__(256) k_init_state(Dev d, const uint8_t *tmp) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     const bool inb = x < d.nx;
     const int i = inb ? cell_index(d, x, y, z) : 0;
-    bool is_if = false;
+    bool is_if = false, obs_nbr = false;
     if (inb) {
         uint8_t t = tmp[i];
-        bool gas_nbr = false, obs_nbr = false;
+        bool gas_nbr = false;
         for (int q = 1; q < Q; ++q) {
             const uint8_t u = tmp[nbr_index(d, x, y, z, cx(q), cy(q), cz(q))];
             gas_nbr |= u == T_GAS;
@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(256) k_init_state(Dev d, const uint8_t *tmp) {
         is_if = t == T_IF;
         if (t & (T_LIQ | T_IF)) d.seg_active[seg_of(d, i)] = 1;
     }
+    if (__any_sync(0xffffffffu, obs_nbr) && (threadIdx.x & 31) == 0) d.counts[C_NEAR] = 1;
     warp_append(d.iflist, d.counts + d.cif, is_if, i);
 }
 
@@ -193,15 +194,15 @@ __global__ void __launch_bounds__(256) k_refresh(Dev d) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     const bool inb = x < d.nx;
     const int i = inb ? cell_index(d, x, y, z) : 0;
-    bool is_if = false;
+    bool is_if = false, obs_nbr = false;
     if (inb) {
         const uint8_t t = d.flags[i] & T_MASK;
-        bool obs_nbr = false;
         for (int q = 1; q < Q; ++q) obs_nbr |= (d.flags[nbr_index(d, x, y, z, cx(q), cy(q), cz(q))] & T_OBS) != 0;
         d.flags[i] = t | (obs_nbr ? B_NEAR : 0);
         is_if = t == T_IF;
         if (t & (T_LIQ | T_IF)) d.seg_active[seg_of(d, i)] = 1;
     }
+    if (__any_sync(0xffffffffu, obs_nbr) && (threadIdx.x & 31) == 0) d.counts[C_NEAR] = 1;
     warp_append(d.iflist, d.counts + d.cif, is_if, i);
 }
 

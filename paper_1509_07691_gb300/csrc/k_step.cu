@@ -196,7 +196,10 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_sc_iface(Dev d) {
 // (as k_lsqr_fast) and, unless the fit defers the cell to the general path,
 // goes straight on with the cell's stream-collide, FSL_IFACE_LANES lanes per
 // cell; k_curv_iface_slow finishes the deferred cells one thread each (Givens
-// fit, FP64 re-solve when ill conditioned, then iface_cell).
+// fit, FP64 re-solve when ill conditioned, then iface_cell).  In a domain
+// without obstacles (no contact lines: a deferral is a rare ill-conditioned
+// or degenerate fit) the fused kernel finishes its deferred cells itself and
+// k_curv_iface_slow is not launched.
 // iface_cell of one cell changes only that cell's transient flag bits, mass,
 // rho and new PDFs, none of which a fit of another cell reads.
 // Lattice directions by pair: pair p (0..8) holds q = 2p + 1 with velocity
@@ -208,6 +211,35 @@ constexpr unsigned PAIR_CZ = 0x37410u;  // p: 0:0 1:0 2:+1 3:0 4:0 5:+1 6:-1 7:+
 __device__ __forceinline__ int pair_c(unsigned packed, int p) {
     const int v = (packed >> (2 * p)) & 3;
     return v == 3 ? -1 : v;
+}
+
+// A cell the fast fit deferred: the streaming Givens fit through accessor acc
+// (re-solved in FP64 when ill conditioned), then the cell's interface
+// stream-collide.
+template <int S, int COLL, class Acc>
+__device__ __forceinline__ void general_cell(const Dev &d, const Acc &acc, int i) {
+    const uint8_t fi = d.flags[i] & (T_MASK | B_NEAR);
+    float cond;
+    float kap = lsqr_core<float>(acc, fi, cond);
+    if (cond * cond > d.fp64_cond) {
+        double c2;
+        kap = (float)lsqr_core<double>(acc, fi, c2);
+        atomicAdd(d.counts + C_FP64, 1);
+    }
+    d.kappa[i] = kap;
+    iface_cell<S, COLL>(d, i);
+}
+
+// the same, by one thread reading the block from global memory: the fused
+// kernel's own deferred cells in a domain without obstacles (no contact
+// lines, so deferrals are rare ill-conditioned fits); out of line, so that the
+// fused kernel's registers are not spent on it
+template <int S, int COLL>
+__device__ __noinline__ void general_cell_grid(const Dev d, int i) {
+    int x, y, z;
+    cell_coords(d, i, x, y, z);
+    const GridAcc acc{d, x, y, z};
+    general_cell<S, COLL>(d, acc, i);
 }
 
 // L lanes per interface cell (a group), rank r = lane % L.  The fit's 27
@@ -432,7 +464,7 @@ __global__ void __launch_bounds__(LIST_BLOCK, IFACE_MIN_BLOCKS) k_curv_iface_fas
             }
         }
         if (act && r == L - 1) St::st(d.fdst, i, 0, fo0 + d.omega_e * ((1.0f / 3.0f) * rg * (1.0f - vv) - fo0), d);
-        warp_append(d.slow, d.counts + C_SLOW, defer && r == 0, i);
+        warp_append(d.slow, d.counts + C_SLOW, defer && r == 0 && !d.inline_general, i);
         if (act && r == 0) {
             d.kappa[i] = kap;
             const float mm = d.mass[i] + dm;
@@ -448,6 +480,7 @@ __global__ void __launch_bounds__(LIST_BLOCK, IFACE_MIN_BLOCKS) k_curv_iface_fas
                 }
             }
         }
+        if (d.inline_general && defer && r == 0) general_cell_grid<S, COLL>(d, i);
     }
 }
 
@@ -471,19 +504,7 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_curv_iface_slow(Dev d) {
         cell_coords(d, i, x, y, z);
         stage_block(d, x, y, z, lane, sfl[w], snm[w]);
         __syncwarp();
-        if (lane == 0) {
-            const StagedAcc acc{d, sfl[w], snm[w]};
-            const uint8_t fi = d.flags[i] & (T_MASK | B_NEAR);
-            float cond;
-            float kap = lsqr_core<float>(acc, fi, cond);
-            if (cond * cond > d.fp64_cond) {
-                double c2;
-                kap = (float)lsqr_core<double>(acc, fi, c2);
-                atomicAdd(d.counts + C_FP64, 1);
-            }
-            d.kappa[i] = kap;
-            iface_cell<S, COLL>(d, i);
-        }
+        if (lane == 0) general_cell<S, COLL>(d, StagedAcc{d, sfl[w], snm[w]}, i);
         __syncwarp();
     }
 }
@@ -858,7 +879,7 @@ void launch_ci(const Dev &d, cudaStream_t s) {
     static const int gf = list_blocks((const void *)k_curv_iface_fast<S, COLL, FSL_IFACE_LANES>, LIST_BLOCK, 4);
     static const int gs = list_blocks((const void *)k_curv_iface_slow<S, COLL>, LIST_BLOCK, 4);
     launch_pdl(k_curv_iface_fast<S, COLL, FSL_IFACE_LANES>, gf, LIST_BLOCK, s, d);
-    launch_pdl(k_curv_iface_slow<S, COLL>, gs, LIST_BLOCK, s, d);
+    if (!d.inline_general) launch_pdl(k_curv_iface_slow<S, COLL>, gs, LIST_BLOCK, s, d);
 }
 
 void launch_sc_bulk(const Dev &d, cudaStream_t s) { FSL_DISPATCH(launch_bulk); }
@@ -873,9 +894,9 @@ void launch_stream_collide(const Dev &d, cudaStream_t s) {
 
 void launch_convert(const Dev &d, cudaStream_t s) {
     switch (d.storage) {
-    case FSL_F32: k_convert<FSL_F32><<<1, CONV_BLOCK, 0, s>>>(d); break;
-    case FSL_F16_OFS: k_convert<FSL_F16_OFS><<<1, CONV_BLOCK, 0, s>>>(d); break;
-    default: k_convert<FSL_BF16_OFS><<<1, CONV_BLOCK, 0, s>>>(d); break;
+    case FSL_F32: launch_pdl(k_convert<FSL_F32>, 1, CONV_BLOCK, s, d); break;
+    case FSL_F16_OFS: launch_pdl(k_convert<FSL_F16_OFS>, 1, CONV_BLOCK, s, d); break;
+    default: launch_pdl(k_convert<FSL_BF16_OFS>, 1, CONV_BLOCK, s, d); break;
     }
 }
 

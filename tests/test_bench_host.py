@@ -39,3 +39,15 @@ def test_zero_crossings_give_the_period_of_a_damped_cosine():
     assert len(zc) == 3
     assert abs(2 * np.mean(np.diff(zc)) - period) < 1e-3 * period
     assert abs(zc[0] - period / 4) < 0.01 * period
+
+
+def test_launches_per_step_follow_the_domain():
+    # LSQR: the general-path kernel is launched only where some cell has an
+    # obstacle neighbour (contact lines); the other models always take 7
+    walls = np.zeros((4, 4, 4), dtype=np.uint8)
+    assert bench.launches_per_step("lsqr", None) == 6
+    assert bench.launches_per_step("lsqr", walls) == 6
+    walls[0] = 1
+    assert bench.launches_per_step("lsqr", walls) == 7
+    assert bench.launches_per_step("fd", None) == 7
+    assert bench.launches_per_step("none", walls) == 7
