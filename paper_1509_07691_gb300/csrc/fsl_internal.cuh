@@ -51,9 +51,11 @@ enum : uint8_t {
 // clears the next step's, and rebuilds the segment list only if it is set)
 enum { C_IF0 = 0, C_IF1 = 1, C_FILL = 2, C_EMPTY = 3, C_NEWGAS = 4, C_LIQ2IF = 5, C_FP64 = 6, C_SEG = 7, C_SLOW = 8,
        C_MLP = 9, C_MLPKEEP = 10, C_ADJ64 = 11, C_SEGD0 = 12, C_SEGD1 = 13, C_ADJGEN = 14, C_NEAR = 15,
-       C_NCOUNT = 16 };
+       C_IFDONE = 16, C_NCOUNT = 17 };
 // C_NEAR is 1 when some cell has an obstacle neighbour (set with the
-// near-obstacle bits at initialisation and refresh; no step changes it)
+// near-obstacle bits at initialisation and refresh; no step changes it);
+// C_IFDONE counts the blocks of the fused fit + interface kernel that have
+// finished (the last one resets it)
 
 // the grid is walked in x-row segments of SEG cells (one warp each); a
 // segment is active while it holds a liquid or interface cell
@@ -129,6 +131,7 @@ struct Dev {
     float fp64_cond;
     // 1: no cell has an obstacle neighbour, so no fit has a contact line and
     // the fused fit + interface kernel finishes its few deferred fits itself
+    // (its last block to finish runs them)
     int inline_general;
     double cos_theta_d, sin_theta_d;
     // learned curvature (FSL_CURV_MLP): packed parameters, judge tolerance
@@ -168,9 +171,9 @@ __device__ __forceinline__ int list_parity(const Dev &d) { return d.cif - C_IF0;
 // non-obstacle cells - liquid cells - interface fill levels of the state the
 // step starts from.
 __device__ __forceinline__ void step_prologue(const Dev &d) {
-    const int zero[8] = {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF, C_SLOW, C_FP64, C_MLP, C_MLPKEEP};
+    const int zero[9] = {C_FILL, C_EMPTY, C_NEWGAS, C_LIQ2IF, C_SLOW, C_FP64, C_MLP, C_MLPKEEP, C_IFDONE};
 #pragma unroll
-    for (int k = 0; k < 8; ++k) d.counts[zero[k]] = 0;
+    for (int k = 0; k < 9; ++k) d.counts[zero[k]] = 0;
     d.counts[d.cif_next] = 0;
     d.counts[d.cdirty_next] = 0;
     if (d.bub_i) {

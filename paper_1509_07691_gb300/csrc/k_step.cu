@@ -198,8 +198,8 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_sc_iface(Dev d) {
 // cell; k_curv_iface_slow finishes the deferred cells one thread each (Givens
 // fit, FP64 re-solve when ill conditioned, then iface_cell).  In a domain
 // without obstacles (no contact lines: a deferral is a rare ill-conditioned
-// or degenerate fit) the fused kernel finishes its deferred cells itself and
-// k_curv_iface_slow is not launched.
+// or degenerate fit) the fused kernel's last block finishes the deferred
+// cells and k_curv_iface_slow is not launched.
 // iface_cell of one cell changes only that cell's transient flag bits, mass,
 // rho and new PDFs, none of which a fit of another cell reads.
 // Lattice directions by pair: pair p (0..8) holds q = 2p + 1 with velocity
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(LIST_BLOCK, IFACE_MIN_BLOCKS) k_curv_iface_fas
             }
         }
         if (act && r == L - 1) St::st(d.fdst, i, 0, fo0 + d.omega_e * ((1.0f / 3.0f) * rg * (1.0f - vv) - fo0), d);
-        warp_append(d.slow, d.counts + C_SLOW, defer && r == 0 && !d.inline_general, i);
+        warp_append(d.slow, d.counts + C_SLOW, defer && r == 0, i);
         if (act && r == 0) {
             d.kappa[i] = kap;
             const float mm = d.mass[i] + dm;
@@ -480,7 +480,22 @@ __global__ void __launch_bounds__(LIST_BLOCK, IFACE_MIN_BLOCKS) k_curv_iface_fas
                 }
             }
         }
-        if (d.inline_general && defer && r == 0) general_cell_grid<S, COLL>(d, i);
+    }
+    // without obstacles the last block to finish runs the deferred fits (rare
+    // ill-conditioned or degenerate ones), one thread per cell: every block's
+    // list appends are fenced before its arrival is counted
+    if (d.inline_general) {  // uniform over the grid
+        __shared__ int last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last = atomicAdd(d.counts + C_IFDONE, 1) == (int)gridDim.x - 1;
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            const int ns = __ldcg(d.counts + C_SLOW);
+            for (int k = threadIdx.x; k < ns; k += blockDim.x) general_cell_grid<S, COLL>(d, __ldcg(d.slow + k));
+            if (threadIdx.x == 0) d.counts[C_IFDONE] = 0;
+        }
     }
 }
 
