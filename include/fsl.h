@@ -148,14 +148,18 @@ int fsl_fill_geometry(const fsl_params *params, const fsl_geometry *geom, float 
  * liquid cell with a gas neighbour becomes interface), f = w_q, m = phi, and
  * the interface list.  fields->f[0] and flags[0] hold the state afterwards;
  * fields->f[1] is a copy of fields->f[0].
- * Asynchronous on `stream` (a cudaStream_t, or NULL for the default stream). */
+ * Queued on `stream` (a cudaStream_t, or NULL for the default stream); returns
+ * after that stream has drained, having read back whether any cell has an
+ * obstacle neighbour (a domain without one runs its rare general-path LSQR
+ * fits inside the fused step kernel instead of a kernel of their own). */
 int fsl_init(const fsl_params *params, const fsl_fields *fields, const float *phi0, int phi0_where,
              const uint8_t *obstacle, int obstacle_where, void *stream, struct fsl_ctx **out);
 
 /* The caller wrote a state directly into f[parity], flags[0] (type bits),
  * mass and phi: recompute the near-obstacle bits, the interface list and the
  * active row segments.
- * Asynchronous. */
+ * Synchronising: returns after the context's stream has drained (it reads
+ * back whether any cell has an obstacle neighbour, as fsl_init). */
 int fsl_refresh(struct fsl_ctx *ctx);
 
 /* Checkpoint and resume (a service of this library; the paper has no
