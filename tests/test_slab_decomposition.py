@@ -174,6 +174,7 @@ def _run(cases, out, world=2):
         return json.load(fh)
 
 
+@pytest.mark.slow
 def test_slab_decomposition_reproduces_the_step(orc, tmp_path):
     # (name, obstacle walls, curvature model, cut axis, ghost layers)
     cases = [("droplet LSQR z", False, 0, 0, 3), ("cap at walls LSQR y", True, 0, 1, 3),
@@ -191,6 +192,7 @@ def test_slab_decomposition_reproduces_the_step(orc, tmp_path):
             assert merr < 1e-12, f"{name}: FP64 mass sum over the ranks off by {merr}"
 
 
+@pytest.mark.slow
 def test_three_slabs(orc, tmp_path):
     """Three ranks: the lower and upper neighbours of a rank differ."""
     cases = [("droplet LSQR z, 3 ranks", False, 0, 0, 3), ("cap at walls FD y, 3 ranks", True, 1, 1, 4)]
